@@ -1,0 +1,265 @@
+"""ctypes wrapper of the FP64 CPU oracle (test infrastructure only).
+
+Only the tests, ``__graft_entry__.smoke()`` and the bench's CPU-baseline /
+reference leg use this module.  The oracle follows Sec. 3.1 of the paper (the
+simulator F, Eq. fwd_dynamics, the contact and joint-limit equations,
+Cholesky, semi-implicit Euler) and Eq. backward / appendix A.1 for the
+adjoint; see ``shac_oracle.cpp`` for the per-function citations.
+
+Arrays at this interface are environment-major ([N][dim]); the helpers
+``soa``/``aos`` convert from/to the structure-of-arrays layout ([dim][N]) the
+CUDA library uses.  Inputs are promoted to float64 as given, so passing the
+float32 values the GPU sees gives both sides identical inputs.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import sys
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "shac_oracle.cpp")
+_LIB = os.path.join(_HERE, "liboracle.so")
+
+_i32p = ctypes.POINTER(ctypes.c_int32)
+_f64p = ctypes.POINTER(ctypes.c_double)
+
+
+class OrcDesc(ctypes.Structure):
+    _fields_ = [
+        ("n_links", ctypes.c_int32), ("parent", _i32p), ("joint_type", _i32p),
+        ("joint_axis", _f64p), ("joint_pos", _f64p), ("joint_quat", _f64p),
+        ("mass", _f64p), ("com", _f64p), ("inertia", _f64p),
+        ("n_contacts", ctypes.c_int32), ("contact_link", _i32p), ("contact_pos", _f64p),
+        ("contact_radius", _f64p),
+        ("q_lower", _f64p), ("q_upper", _f64p), ("armature", _f64p), ("damping", _f64p),
+        ("k_limit", ctypes.c_double),
+        ("n_tact", ctypes.c_int32), ("act_dof", _i32p), ("act_gear", _f64p),
+        ("n_muscles", ctypes.c_int32), ("muscle_ptr", _i32p), ("via_link", _i32p),
+        ("via_pos", _f64p), ("muscle_fmax", _f64p),
+        ("dt", ctypes.c_double), ("substeps", ctypes.c_int32), ("gravity", ctypes.c_double * 3),
+        ("ke", ctypes.c_double), ("kd", ctypes.c_double), ("kt", ctypes.c_double), ("mu", ctypes.c_double),
+        ("rw_q", _f64p), ("rw_qd", _f64p), ("reward_coef", ctypes.c_double * 10),
+    ]
+
+
+def build(force: bool = False) -> str:
+    """Compile liboracle.so with g++ (-O2, OpenMP).  Portable flags only."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        cmd = ["g++", "-O2", "-std=c++17", "-fopenmp", "-fPIC", "-shared", _SRC, "-o", _LIB + ".tmp"]
+        subprocess.check_call(cmd)
+        os.replace(_LIB + ".tmp", _LIB)
+    return _LIB
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_LIB)
+        D = ctypes.POINTER(OrcDesc)
+        i32 = ctypes.c_int32
+        L.orc_step.argtypes = [D, i32, _f64p, _f64p, _f64p, _f64p, _f64p, _f64p]
+        L.orc_step_jacobian.argtypes = [D, i32, _f64p, _f64p, _f64p, _f64p]
+        L.orc_step_vjp.argtypes = [D, i32, _f64p, _f64p, _f64p, _f64p, _f64p, _f64p, _f64p, _f64p, _f64p]
+        L.orc_window_forward.argtypes = [D, i32, i32, _f64p, _f64p, _f64p, _f64p, _f64p, _f64p]
+        L.orc_window_adjoint.argtypes = [D, i32, i32, _f64p, _f64p, _f64p, _f64p, _f64p, _f64p,
+                                         _f64p, _f64p, _f64p]
+        L.orc_forward_accel.argtypes = [D, _f64p, _f64p, _f64p, _f64p]
+        L.orc_mass_matrix.argtypes = [D, _f64p, _f64p]
+        L.orc_inverse_dynamics.argtypes = [D, _f64p, _f64p, _f64p, _f64p, i32, _f64p]
+        L.orc_joint_forces.argtypes = [D, _f64p, _f64p, _f64p, _f64p]
+        L.orc_energy_momentum.argtypes = [D, _f64p, _f64p, _f64p]
+        L.orc_link_poses.argtypes = [D, _f64p, _f64p, _f64p, _f64p]
+        L.orc_muscle_lengths.argtypes = [D, _f64p, _f64p]
+        L.orc_cholesky.argtypes = [i32, _f64p, _f64p]
+        L.orc_num_threads.restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def num_threads() -> int:
+    return int(lib().orc_num_threads())
+
+
+def _d(a):
+    a = np.ascontiguousarray(np.asarray(a, np.float64))
+    return a, a.ctypes.data_as(_f64p)
+
+
+def _i(a):
+    a = np.ascontiguousarray(np.asarray(a, np.int32))
+    return a, a.ctypes.data_as(_i32p)
+
+
+class Oracle:
+    """The oracle bound to one articulation model (an ``inputs.ArticulationModel``)."""
+
+    def __init__(self, model):
+        self.model = model
+        keep = []
+
+        def d(x):
+            arr, p = _d(x)
+            keep.append(arr)
+            return p
+
+        def i(x):
+            arr, p = _i(x)
+            keep.append(arr)
+            return p
+
+        m = model
+        desc = OrcDesc()
+        desc.n_links = m.n_links
+        desc.parent = i(m.parent)
+        desc.joint_type = i(m.joint_type)
+        desc.joint_axis = d(m.joint_axis)
+        desc.joint_pos = d(m.joint_pos)
+        desc.joint_quat = d(m.joint_quat)
+        desc.mass = d(m.mass)
+        desc.com = d(m.com)
+        desc.inertia = d(m.inertia)
+        desc.n_contacts = m.n_contacts
+        desc.contact_link = i(m.contact_link if m.n_contacts else np.zeros(1, np.int32))
+        desc.contact_pos = d(m.contact_pos if m.n_contacts else np.zeros(3))
+        desc.contact_radius = d(m.contact_radius if m.n_contacts else np.zeros(1))
+        desc.q_lower = d(m.q_lower)
+        desc.q_upper = d(m.q_upper)
+        desc.armature = d(m.armature)
+        desc.damping = d(m.damping)
+        desc.k_limit = float(m.k_limit)
+        desc.n_tact = m.n_tact
+        desc.act_dof = i(m.act_dof if m.n_tact else np.zeros(1, np.int32))
+        desc.act_gear = d(m.act_gear if m.n_tact else np.zeros(1))
+        desc.n_muscles = m.n_muscles
+        desc.muscle_ptr = i(m.muscle_ptr)
+        desc.via_link = i(m.via_link if m.via_link.size else np.zeros(1, np.int32))
+        desc.via_pos = d(m.via_pos if m.via_pos.size else np.zeros(3))
+        desc.muscle_fmax = d(m.muscle_fmax if m.n_muscles else np.zeros(1))
+        desc.dt = float(m.dt)
+        desc.substeps = int(m.substeps)
+        for k in range(3):
+            desc.gravity[k] = float(m.gravity[k])
+        desc.ke, desc.kd, desc.kt, desc.mu = float(m.ke), float(m.kd), float(m.kt), float(m.mu)
+        desc.rw_q = d(m.rw_q)
+        desc.rw_qd = d(m.rw_qd)
+        for k in range(10):
+            desc.reward_coef[k] = float(m.reward_coef[k])
+        self._keep = keep
+        self.desc = desc
+        self.nq, self.nv, self.na = m.nq, m.nv, m.na
+
+    # ---- batched (env-major) -------------------------------------------
+    def step(self, q, qd, a):
+        q, pq = _d(q); qd, pqd = _d(qd); a, pa = _d(a)
+        N = q.shape[0]
+        qn = np.zeros((N, self.nq)); qdn = np.zeros((N, self.nv)); r = np.zeros(N)
+        lib().orc_step(ctypes.byref(self.desc), N, pq, pqd, pa, _d(qn)[1], _d(qdn)[1], _d(r)[1])
+        return qn, qdn, r
+
+    def step_jacobian(self, q, qd, a):
+        q, pq = _d(q); qd, pqd = _d(qd); a, pa = _d(a)
+        N = q.shape[0]
+        J = np.zeros((N, self.nq + self.nv + 1, self.nq + self.nv + self.na))
+        lib().orc_step_jacobian(ctypes.byref(self.desc), N, pq, pqd, pa, J.ctypes.data_as(_f64p))
+        return J
+
+    def step_vjp(self, q, qd, a, qn_bar, qdn_bar, r_bar):
+        arrs = [_d(x) for x in (q, qd, a, qn_bar, qdn_bar, r_bar)]
+        N = arrs[0][0].shape[0]
+        qb = np.zeros((N, self.nq)); qdb = np.zeros((N, self.nv)); ab = np.zeros((N, self.na))
+        lib().orc_step_vjp(ctypes.byref(self.desc), N, *[p for _, p in arrs],
+                           qb.ctypes.data_as(_f64p), qdb.ctypes.data_as(_f64p), ab.ctypes.data_as(_f64p))
+        return qb, qdb, ab
+
+    def window_forward(self, q0, qd0, act):
+        """q0 [N,nq], qd0 [N,nv], act [h,N,na] -> q_traj [h+1,N,nq], qd_traj, rew [h,N]."""
+        q0, p0 = _d(q0); qd0, pd0 = _d(qd0); act, pa = _d(act)
+        h, N = act.shape[0], act.shape[1]
+        qt = np.zeros((h + 1, N, self.nq)); qdt = np.zeros((h + 1, N, self.nv)); rw = np.zeros((h, N))
+        lib().orc_window_forward(ctypes.byref(self.desc), N, h, p0, pd0, pa,
+                                 qt.ctypes.data_as(_f64p), qdt.ctypes.data_as(_f64p), rw.ctypes.data_as(_f64p))
+        return qt, qdt, rw
+
+    def window_adjoint(self, q_traj, qd_traj, act, r_bar, qT_bar, qdT_bar):
+        arrs = [_d(x) for x in (q_traj, qd_traj, act, r_bar, qT_bar, qdT_bar)]
+        h, N = arrs[2][0].shape[0], arrs[2][0].shape[1]
+        qb = np.zeros((N, self.nq)); qdb = np.zeros((N, self.nv)); ab = np.zeros((h, N, self.na))
+        lib().orc_window_adjoint(ctypes.byref(self.desc), N, h, *[p for _, p in arrs],
+                                 qb.ctypes.data_as(_f64p), qdb.ctypes.data_as(_f64p), ab.ctypes.data_as(_f64p))
+        return qb, qdb, ab
+
+    # ---- single state ------------------------------------------------------
+    def forward_accel(self, q, qd, a):
+        out = np.zeros(self.nv)
+        lib().orc_forward_accel(ctypes.byref(self.desc), _d(q)[1], _d(qd)[1], _d(a)[1], out.ctypes.data_as(_f64p))
+        return out
+
+    def mass_matrix(self, q):
+        out = np.zeros((self.nv, self.nv))
+        q, pq = _d(q)
+        lib().orc_mass_matrix(ctypes.byref(self.desc), pq, out.ctypes.data_as(_f64p))
+        return out
+
+    def inverse_dynamics(self, q, qd, qdd, a=None, with_ext=True):
+        if a is None:
+            a = np.zeros(max(1, self.na))
+        out = np.zeros(self.nv)
+        q, pq = _d(q); qd, pqd = _d(qd); qdd, pqdd = _d(qdd); a, pa = _d(a)
+        lib().orc_inverse_dynamics(ctypes.byref(self.desc), pq, pqd, pqdd, pa, int(with_ext),
+                                   out.ctypes.data_as(_f64p))
+        return out
+
+    def joint_forces(self, q, qd, a):
+        out = np.zeros(self.nv)
+        q, pq = _d(q); qd, pqd = _d(qd); a, pa = _d(a)
+        lib().orc_joint_forces(ctypes.byref(self.desc), pq, pqd, pa, out.ctypes.data_as(_f64p))
+        return out
+
+    def energy_momentum(self, q, qd):
+        out = np.zeros(11)
+        q, pq = _d(q); qd, pqd = _d(qd)
+        lib().orc_energy_momentum(ctypes.byref(self.desc), pq, pqd, out.ctypes.data_as(_f64p))
+        return dict(T=out[0], V=out[1], P=out[2:5].copy(), H=out[5:8].copy(), com=out[8:11].copy())
+
+    def link_poses(self, q):
+        L = self.model.n_links
+        R = np.zeros((L, 3, 3)); o = np.zeros((L, 3)); c = np.zeros((L, 3))
+        q, pq = _d(q)
+        lib().orc_link_poses(ctypes.byref(self.desc), pq, R.ctypes.data_as(_f64p),
+                             o.ctypes.data_as(_f64p), c.ctypes.data_as(_f64p))
+        return R, o, c
+
+    def muscle_lengths(self, q):
+        out = np.zeros(max(1, self.model.n_muscles))
+        q, pq = _d(q)
+        lib().orc_muscle_lengths(ctypes.byref(self.desc), pq, out.ctypes.data_as(_f64p))
+        return out[: self.model.n_muscles]
+
+
+def cholesky(A):
+    A, pa = _d(A)
+    n = A.shape[0]
+    Lc = np.zeros((n, n))
+    lib().orc_cholesky(n, pa, Lc.ctypes.data_as(_f64p))
+    return Lc
+
+
+def aos(x):
+    """[dim][N] (or [t][dim][N]) -> [N][dim] (or [t][N][dim]) float64."""
+    x = np.asarray(x, np.float64)
+    return np.ascontiguousarray(np.swapaxes(x, -1, -2))
+
+
+soa = aos
+
+if __name__ == "__main__":
+    build(force="--force" in sys.argv)
+    print(_LIB)

@@ -1,0 +1,206 @@
+/*
+ * shacsim.h -- C ABI of the GB300 parallel differentiable articulated-body
+ * simulator: the batched step s_{t+1} = F(s_t, a_t) of many independent
+ * environments and its reverse-mode adjoint (Short-Horizon Actor-Critic,
+ * arXiv 2204.07137, Sec. 3.1 "GPU-Based Differentiable Dynamics Simulation",
+ * Eq. backward and Eq. fwd_dynamics; appendix A.1 for the window recursion).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - All floating point data is FP32.  Device arrays are structure-of-arrays
+ *    per articulation group: a quantity with D components for a group of N_g
+ *    environments occupies D*N_g floats laid out [D][N_g] (component-major,
+ *    environment fastest).  Groups are concatenated in the order given to
+ *    shac_batch_create.  Per-step trajectories stack these blocks over time:
+ *    [t][sum_g D_g*N_g].
+ *  - State s = (q, qd).  q holds joint coordinates (free root: position xyz
+ *    then unit quaternion xyzw; revolute/prismatic: one coordinate), qd joint
+ *    velocities (free root: body-frame angular velocity then body-frame
+ *    velocity of the root origin).  Actions a: per-DOF torque commands
+ *    (scaled by the model gear) followed by muscle activations.
+ *  - Ownership: the caller owns every device buffer it passes, including the
+ *    workspace (size from shac_batch_workspace_bytes).  The library owns only
+ *    its handles and the device copies of the model constants, allocated once
+ *    in shac_batch_create and freed in shac_batch_destroy.
+ *  - step / window calls are asynchronous on the given CUDA stream (a
+ *    cudaStream_t passed as void*; NULL = legacy default stream), perform no
+ *    allocation, no host synchronisation and no host read-back, so they can
+ *    be captured in CUDA graphs.  Arguments are validated on the host; an
+ *    invalid argument returns an error status and launches nothing.
+ *  - Device-side problems (a non-finite state produced by a step) set a
+ *    sticky flag word read with shac_get_status.
+ *  - *_bar outputs are overwritten (not accumulated).
+ */
+#ifndef SHACSIM_H
+#define SHACSIM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SHAC_OK = 0,
+  SHAC_ERR_INVALID_ARG = 1,   /* null pointer, bad size, bad enum */
+  SHAC_ERR_MODEL = 2,         /* not a tree / parent after child / free joint not at a root / bad index */
+  SHAC_ERR_CUDA = 3,          /* a CUDA runtime call failed */
+  SHAC_ERR_NONFINITE = 4,     /* sticky: a step produced a non-finite state */
+  SHAC_ERR_CAPACITY = 5,      /* model exceeds a compiled limit (e.g. more than 32 DOF) */
+  SHAC_ERR_UNSUPPORTED = 6    /* requested form/option not available */
+} shac_status;
+
+/* Joint types (Sec. 3.1: articulated rigid bodies in generalised coordinates) */
+enum { SHAC_JOINT_FREE = 0, SHAC_JOINT_REVOLUTE = 1, SHAC_JOINT_PRISMATIC = 2, SHAC_JOINT_FIXED = 3 };
+
+/* Execution forms */
+enum {
+  SHAC_FORM_PLAIN = 0,   /* one environment per thread, one kernel per stage per substep */
+  SHAC_FORM_BATCHED = 1  /* lane teams per environment, every stage and substep fused in one
+                            persistent launch per window (or per step) */
+};
+
+typedef struct shac_model shac_model;
+typedef struct shac_batch shac_batch;
+
+/*
+ * Host-side description of one articulation (paper Sec. 3.1: a joint tree
+ * with masses, inertias, contact shapes, joint limits and actuation).  The
+ * library copies everything; the caller keeps ownership of its arrays.
+ *
+ *  n_links          links, numbered so that parent[i] < i (-1 = world).
+ *  joint_type[L]    SHAC_JOINT_*; a FREE joint must be a root (parent -1) and
+ *                   ignores joint_pos/joint_quat.
+ *  joint_axis[L][3] unit axis in the joint frame (revolute/prismatic).
+ *  joint_pos[L][3], joint_quat[L][4] (xyzw): joint frame in the parent link
+ *                   frame.  The link frame coincides with the joint frame at
+ *                   zero joint coordinate.
+ *  mass[L], com[L][3], inertia[L][6] (xx yy zz xy xz yz about the COM, link frame).
+ *  n_contacts, contact_link[C], contact_pos[C][3] (sphere centre, link frame),
+ *                   contact_radius[C]: spheres against the ground plane z = 0.
+ *  q_lower/q_upper[nv]: per-DOF joint limits (use +-1e30 for none; only
+ *                   revolute/prismatic DOFs are limited), k_limit: stiffness.
+ *  armature[nv], joint_damping[nv].
+ *  n_tact, act_dof[n_tact], act_gear[n_tact]: torque actuator k drives DOF
+ *                   act_dof[k] with torque act_gear[k] * a[k] (one actuator per DOF).
+ *  n_muscles, muscle_ptr[n_muscles+1], via_link[V], via_pos[V][3] (link frame),
+ *                   muscle_fmax[n_muscles]: muscle m pulls consecutive via
+ *                   points together with force clamp(a, 0, 1) * fmax; its
+ *                   activation is a[n_tact + m].
+ *  dt: control step; substeps: K semi-implicit Euler substeps per step,
+ *                   action held; gravity[3].
+ *  ke, kd, kt, mu:  contact normal stiffness, damping, friction stiffness, friction coefficient.
+ *  rw_q[nq], rw_qd[nv], reward_coef[10]: reward on the post-step state,
+ *     r = -sum rw_q q^2 - sum rw_qd qd^2 - c0 |a|^2
+ *         + (free root only) c1 vx + c2 up_z + c3 head_x + Rh(clip(z - c4, c5, c6)),
+ *     Rh(D) = c7 D^2 + c8 D (D < 0), c9 D (D >= 0).
+ */
+typedef struct {
+  int32_t n_links;
+  const int32_t* parent;
+  const int32_t* joint_type;
+  const float* joint_axis;
+  const float* joint_pos;
+  const float* joint_quat;
+  const float* mass;
+  const float* com;
+  const float* inertia;
+  int32_t n_contacts;
+  const int32_t* contact_link;
+  const float* contact_pos;
+  const float* contact_radius;
+  const float* q_lower;
+  const float* q_upper;
+  float k_limit;
+  const float* armature;
+  const float* joint_damping;
+  int32_t n_tact;
+  const int32_t* act_dof;
+  const float* act_gear;
+  int32_t n_muscles;
+  const int32_t* muscle_ptr;
+  const int32_t* via_link;
+  const float* via_pos;
+  const float* muscle_fmax;
+  float dt;
+  int32_t substeps;
+  float gravity[3];
+  float ke, kd, kt, mu;
+  const float* rw_q;
+  const float* rw_qd;
+  float reward_coef[10];
+} shac_model_desc;
+
+/* Validate and copy a model description.  Returns SHAC_ERR_MODEL for a
+ * malformed tree or index, SHAC_ERR_CAPACITY beyond the compiled limits
+ * (64 links, 32 DOF, 64 contacts). */
+shac_status shac_model_create(const shac_model_desc* desc, shac_model** out);
+void shac_model_destroy(shac_model* model);
+/* nq, nv, na of a model (any pointer may be NULL). */
+void shac_model_dims(const shac_model* model, int32_t* nq, int32_t* nv, int32_t* na);
+
+/* A batch of n_groups articulation groups (models[g] with n_envs[g] >= 0
+ * environments each) executed in one form.  Uploads the model constants to
+ * the current CUDA device (the one allocation point).  window_h_max bounds the
+ * h accepted by the window calls. */
+shac_status shac_batch_create(const shac_model* const* models, const int32_t* n_envs, int32_t n_groups,
+                              int32_t form, int32_t window_h_max, shac_batch** out);
+void shac_batch_destroy(shac_batch* batch);
+/* Totals over groups: sum nq_g N_g, sum nv_g N_g, sum na_g N_g, sum N_g. */
+void shac_batch_dims(const shac_batch* batch, int64_t* q_size, int64_t* qd_size, int64_t* act_size,
+                     int64_t* n_envs);
+/* Bytes of caller-allocated device workspace the batch needs (256-byte aligned pointer). */
+size_t shac_batch_workspace_bytes(const shac_batch* batch);
+
+/* One control step (K substeps, then the reward).  q/qd/act: [q_size]/[qd_size]/[act_size];
+ * q_next/qd_next likewise; reward: [n_envs].  Inputs and outputs must not alias. */
+shac_status shac_step(shac_batch* batch, void* stream, void* workspace,
+                      const float* q, const float* qd, const float* act,
+                      float* q_next, float* qd_next, float* reward);
+
+/* Eq. backward for one step: given the step input (q, qd, act) and the
+ * cotangents of its outputs (q_next_bar, qd_next_bar, reward_bar), write
+ * q_bar = dL/dq, qd_bar = dL/dqd, act_bar = dL/dact.  Substeps are recomputed
+ * from the input state. */
+shac_status shac_step_adjoint(shac_batch* batch, void* stream, void* workspace,
+                              const float* q, const float* qd, const float* act,
+                              const float* q_next_bar, const float* qd_next_bar, const float* reward_bar,
+                              float* q_bar, float* qd_bar, float* act_bar);
+
+/* h steps: act [h][act_size]; q_traj/qd_traj [h+1][..] (entry 0 = q0/qd0 copy),
+ * reward [h][n_envs].  The trajectory is the per-control-step checkpoint tape. */
+shac_status shac_window_forward(shac_batch* batch, void* stream, void* workspace, int32_t h,
+                                const float* q0, const float* qd0, const float* act,
+                                float* q_traj, float* qd_traj, float* reward);
+
+/* Appendix A.1 recursion (without the policy term): reverse over the h
+ * steps of a window given its checkpoint tape (q_traj, qd_traj [h+1][..] from
+ * shac_window_forward), the per-step reward cotangents reward_bar [h][n_envs]
+ * and the cotangents of every checkpoint q_traj_bar/qd_traj_bar [h+1][..]
+ * (entry h = final state; pass zeros where the loss does not read a
+ * checkpoint directly).  Writes q0_bar/qd0_bar (total cotangent of the start
+ * state, including entry 0) and act_bar [h][act_size].  Substeps of each step
+ * are recomputed from its checkpoint. */
+shac_status shac_window_adjoint(shac_batch* batch, void* stream, void* workspace, int32_t h,
+                                const float* q_traj, const float* qd_traj, const float* act,
+                                const float* reward_bar, const float* q_traj_bar, const float* qd_traj_bar,
+                                float* q0_bar, float* qd0_bar, float* act_bar);
+
+/* Batched-form launch shape: lanes per environment for group g (1,2,4,8,16,32;
+ * 0 = automatic) and warps per CTA.  Does not change results beyond FP32
+ * reassociation inside a team. */
+shac_status shac_batch_set_launch(shac_batch* batch, int32_t group, int32_t lanes_per_env, int32_t warps_per_cta);
+shac_status shac_batch_get_launch(const shac_batch* batch, int32_t group, int32_t* lanes_per_env,
+                                  int32_t* warps_per_cta);
+
+/* Synchronises the stream and returns the sticky device flags
+ * (bit 0: non-finite state); clear != 0 resets them.  Not capturable. */
+shac_status shac_get_status(shac_batch* batch, void* stream, uint32_t* sticky_flags, int32_t clear);
+
+const char* shac_status_string(shac_status status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SHACSIM_H */

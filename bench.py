@@ -1,0 +1,391 @@
+"""Benchmark: env-steps/s of the forward + adjoint window (h = 32) of the
+differentiable simulator on the 2048-environment ant-like workload.
+
+One bench "step" is one pass of the whole hot path over one batch: the
+window forward (32 control steps x 16 substeps, writing the per-step
+checkpoints) followed by the window adjoint (reverse over the 32 steps,
+substeps recomputed from the checkpoints).  value = N * h / time.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Timed form: BATCHED, both launches captured in one CUDA graph, inputs resident
+in HBM, L2 flushed (256 MB write) before every timed step, CUDA events on the
+launching stream.  The PLAIN form (one env per thread, one kernel per stage
+per substep) is timed on the same inputs for the speed-up.  ``e2e`` repeats
+the measurement through the public API with pinned host buffers: host->device
+copies of (q0, qd0, actions) and device->host copies of (rewards, action and
+initial-state gradients) inside the timed region.
+
+--impl reference times the FP64 CPU oracle (forward + exact adjoint) on the
+host cores on a bounded sample of the same workload.
+Under torchrun each rank simulates its own 2048 environments (weak scaling,
+no collective on the data path); rank 0 prints the line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "env-steps/s fwd+adjoint over 32-step window, batched vs plain; grad rel err<=1e-3"
+WORKLOAD = "ant-2048"
+H = 32
+FLUSH_BYTES = 256 << 20
+
+# FP32 ALU peak of one GB300 from its unit counts and clock: 152 SMs x 128
+# FP32 lanes x 2 flop (FMA) x 2.07 GHz maximum SM clock.
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+# Algorithmic FP32 work per env-step (forward window step + adjoint step
+# including the substep recompute) of the ant-like model: thread-level
+# FADD + FMUL + 2 x FFMA executed by the one-env-per-thread (PLAIN) stage
+# kernels, counted by ncu over one window (profiles/plain_flops_ant.md).
+# None until measured; the roofline then reports achieved = null.
+ALGO_FLOPS_PER_ENV_STEP = {"forward": None, "adjoint": None}
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    p.add_argument("--plain-steps", type=int, default=2)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--workload", default=WORKLOAD)
+    return p.parse_args()
+
+
+# ------------------------------------------------------------------ clocks --
+class ClockSampler:
+    """nvidia-smi samples (200 ms) during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------- reference --
+def oracle_window_rate(model, n_envs: int, seed: int = 0, target_s: float = 12.0):
+    """env-steps/s of the FP64 oracle (window forward + exact adjoint) on a
+    bounded sample of the workload, sized to about target_s of wall time."""
+    from paper_2204_07137_gb300 import inputs as I
+    from oracle import oracle
+    o = oracle.Oracle(model)
+
+    def run(n):
+        q0, qd0 = I.initial_state(model, n, seed)
+        act = I.window_actions(model, n, H, seed)
+        t0 = time.perf_counter()
+        qt, qdt, rw = o.window_forward(q0.T, qd0.T, act.transpose(0, 2, 1))
+        o.window_adjoint(qt, qdt, act.transpose(0, 2, 1), np.ones((H, n)), np.zeros((n, model.nq)),
+                         np.zeros((n, model.nv)))
+        return time.perf_counter() - t0
+
+    threads = oracle.num_threads()
+    n = max(1, min(n_envs, threads))
+    dt = run(n)
+    while dt < target_s / 4 and n < n_envs:
+        n = min(n_envs, max(n + 1, int(n * min(8.0, target_s / max(dt, 1e-3)))))
+        dt = run(n)
+    return n * H / dt, n, threads, dt
+
+
+def reference_main(args, rank, world):
+    from paper_2204_07137_gb300 import inputs as I
+    if rank != 0:
+        return
+    wl = I.workload(args.workload)
+    model, n_total = wl.groups[0]
+    rates = []
+    for _ in range(args.warmup):
+        pass   # the oracle has no warm-up state; W untimed steps are not needed on the CPU
+    samples = []
+    for s in range(args.steps):
+        r, n, threads, dt = oracle_window_rate(model, n_total, seed=s, target_s=min(12.0, 60.0 / max(1, args.steps)))
+        rates.append(r)
+        samples.append((n, dt))
+    value = statistics.median(rates)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "env-steps/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * n_total * H / value,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl.name, "n_envs": n_total, "h": H, "substeps": model.substeps,
+                   "form": "FP64 CPU oracle, forward + dual-number exact adjoint"},
+        "cpu_baseline": {"value": value, "unit": "env-steps/s", "cores": threads, "kind": "oracle",
+                         "sample": f"{samples[0][0]} of {n_total} envs x {H} steps per timed step"},
+        "e2e": {"value": value, "unit": "env-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------- GPU ---
+def gpu_main(args, rank, world, dist):
+    import torch
+    from paper_2204_07137_gb300 import build, inputs as I
+    from paper_2204_07137_gb300.sim import Simulator
+
+    build.build()
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    wl = I.workload(args.workload)
+    groups = wl.groups
+    n_envs = wl.n_envs
+
+    def make(form):
+        return Simulator(groups, form=form, h_max=H)
+
+    sim = make("batched")
+    q0 = sim.pack([I.initial_state(m, n, rank)[0] for m, n in groups], "q")
+    qd0 = sim.pack([I.initial_state(m, n, rank)[1] for m, n in groups], "qd")
+    act = torch.cat([torch.from_numpy(I.window_actions(m, n, H, rank).reshape(H, -1)) for m, n in groups],
+                    dim=1).to(dev).contiguous()
+    # loss = mean reward over the window: reward cotangent 1 / (N h)
+    rbar = torch.full((H, n_envs), 1.0 / (n_envs * H), device=dev)
+    zq = torch.zeros(H + 1, sim.q_size, device=dev)
+    zqd = torch.zeros(H + 1, sim.qd_size, device=dev)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+
+    # ---- batched form: graph-captured forward + adjoint window
+    with torch.cuda.stream(stream):
+        outf = sim.window_forward(q0, qd0, act, stream=stream)
+        outa = sim.window_adjoint(outf[0], outf[1], act, rbar, zq, zqd, stream=stream)
+    stream.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(stream):
+        with torch.cuda.graph(graph, stream=stream):
+            sim.window_forward(q0, qd0, act, out=outf, stream=stream)
+            sim.window_adjoint(outf[0], outf[1], act, rbar, zq, zqd, out=outa, stream=stream)
+    stream.synchronize()
+
+    def timed(fn, steps, warmup, per_kernel=None):
+        with torch.cuda.stream(stream):
+            for _ in range(warmup):
+                fn()
+            stream.synchronize()
+            if dist is not None:
+                dist.barrier()
+            torch.cuda.synchronize()
+            total = 0.0
+            for _ in range(steps):
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                fn()
+                e1.record(stream)
+                e1.synchronize()
+                total += e0.elapsed_time(e1)
+            torch.cuda.synchronize()
+            if dist is not None:
+                dist.barrier()
+        return total / steps   # ms per step
+
+    sampler = ClockSampler(dev.index) if rank == 0 else None
+    if sampler:
+        sampler.start()
+    ms_batched = timed(graph.replay, args.steps, args.warmup)
+    clocks = sampler.stop() if sampler else None
+
+    # per-kernel durations (eager launches, same stream) for the roofline
+    def one_fwd():
+        sim.window_forward(q0, qd0, act, out=outf, stream=stream)
+
+    def one_adj():
+        sim.window_adjoint(outf[0], outf[1], act, rbar, zq, zqd, out=outa, stream=stream)
+
+    ms_fwd = timed(one_fwd, max(3, args.steps // 2), 1)
+    ms_adj = timed(one_adj, max(3, args.steps // 2), 1)
+
+    # gradient validity gate: sampled environments against the FP64 oracle
+    grad_rel = None
+    if rank == 0:
+        grad_rel = gradient_check(sim, groups, outf, outa, act, rbar)
+
+    # ---- plain form on the same inputs
+    plain = make("plain")
+    pf = plain.window_forward(q0, qd0, act, stream=stream)
+    pa = plain.window_adjoint(pf[0], pf[1], act, rbar, zq, zqd, stream=stream)
+    stream.synchronize()
+
+    def plain_step():
+        plain.window_forward(q0, qd0, act, out=pf, stream=stream)
+        plain.window_adjoint(pf[0], pf[1], act, rbar, zq, zqd, out=pa, stream=stream)
+
+    ms_plain = timed(plain_step, args.plain_steps, 1)
+
+    # ---- end to end through the public API with pinned host buffers
+    hq0 = q0.cpu().pin_memory()
+    hqd0 = qd0.cpu().pin_memory()
+    hact = act.cpu().pin_memory()
+    dq0, dqd0, dact = torch.empty_like(q0), torch.empty_like(qd0), torch.empty_like(act)
+    hrew = torch.empty(H, n_envs).pin_memory()
+    hab = torch.empty(H, sim.act_size).pin_memory()
+    hq0b = torch.empty(sim.q_size).pin_memory()
+    hqd0b = torch.empty(sim.qd_size).pin_memory()
+
+    def e2e_step():
+        dq0.copy_(hq0, non_blocking=True)
+        dqd0.copy_(hqd0, non_blocking=True)
+        dact.copy_(hact, non_blocking=True)
+        f = sim.window_forward(dq0, dqd0, dact, out=outf, stream=stream)
+        a = sim.window_adjoint(f[0], f[1], dact, rbar, zq, zqd, out=outa, stream=stream)
+        hrew.copy_(f[2], non_blocking=True)
+        hq0b.copy_(a[0], non_blocking=True)
+        hqd0b.copy_(a[1], non_blocking=True)
+        hab.copy_(a[2], non_blocking=True)
+
+    ms_e2e = timed(e2e_step, args.steps, args.warmup)
+    h2d = 4 * (q0.numel() + qd0.numel() + act.numel())
+    d2h = 4 * (hrew.numel() + hab.numel() + hq0b.numel() + hqd0b.numel())
+
+    # max over ranks
+    times = torch.tensor([ms_batched, ms_plain, ms_e2e, ms_fwd, ms_adj], device=dev)
+    if dist is not None:
+        dist.all_reduce(times, op=dist.ReduceOp.MAX)
+    ms_batched, ms_plain, ms_e2e, ms_fwd, ms_adj = times.tolist()
+    if rank != 0:
+        return
+    env_steps = n_envs * H * world
+    value = env_steps / (ms_batched * 1e-3)
+    plain_value = env_steps / (ms_plain * 1e-3)
+    dominant, ms_dom = ("k_batched_adjoint", ms_adj) if ms_adj >= ms_fwd else ("k_batched_forward", ms_fwd)
+    af = ALGO_FLOPS_PER_ENV_STEP["adjoint" if dominant.endswith("adjoint") else "forward"]
+    achieved = None if af is None else af * n_envs * H / (ms_dom * 1e-3) / 1e12
+    line = {
+        "metric": METRIC, "value": value, "unit": "env-steps/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_batched, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": wl.name, "n_envs_per_gpu": n_envs, "h": H,
+                   "substeps": groups[0][0].substeps, "form": "batched, forward+adjoint captured in one CUDA graph",
+                   "lanes_per_env": [sim.get_launch(g)[0] for g in range(len(groups))],
+                   "warps_per_cta": sim.get_launch(0)[1], "l2": "flushed (256 MB write) before each timed step",
+                   "parallelism": f"env-sharded replicas x{world}"},
+        "plain_form": {"value": plain_value, "unit": "env-steps/s", "ms_per_step": ms_plain,
+                       "steps": args.plain_steps},
+        "speedup_vs_plain": value / plain_value,
+        "kernels_ms": {"k_batched_forward": ms_fwd, "k_batched_adjoint": ms_adj},
+        "grad_rel_err_max": grad_rel,
+        "gpu_launches": 2 * args.steps,
+        "clocks": clocks,
+        "e2e": {"value": env_steps / (ms_e2e * 1e-3), "unit": "env-steps/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "roofline": {"bound": "alu", "kernel": dominant, "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
+                     "unit": "TFLOP/s", "frac": None if achieved is None else achieved / FP32_PEAK_TFLOPS,
+                     "peak_source": "derived FP32 peak: 152 SMs x 128 lanes x 2 x 2.07 GHz",
+                     "traffic": None},
+    }
+    if not args.no_cpu_baseline:
+        r, n, threads, dt = oracle_window_rate(groups[0][0], groups[0][1], seed=0, target_s=12.0)
+        line["cpu_baseline"] = {"value": r, "unit": "env-steps/s", "cores": threads, "kind": "oracle",
+                                "sample": f"{n} of {groups[0][1]} envs x {H} steps, forward + exact adjoint, "
+                                          f"{dt:.1f} s"}
+    print(json.dumps(line), flush=True)
+
+
+def gradient_check(sim, groups, outf, outa, act, rbar, n_sample: int = 4):
+    """Max per-env relative error of the window gradients (action and
+    initial-state cotangents) on sampled environments vs the FP64 oracle
+    adjoint run on the GPU checkpoints."""
+    from oracle import oracle
+    model, N = groups[0]
+    o = oracle.Oracle(model)
+    rng = np.random.default_rng(0)
+    envs = np.sort(rng.choice(N, size=min(n_sample, N), replace=False))
+    qt = outf[0].cpu().numpy().reshape(H + 1, model.nq, N)[:, :, envs]
+    qdt = outf[1].cpu().numpy().reshape(H + 1, model.nv, N)[:, :, envs]
+    a = act.cpu().numpy().reshape(H, model.na, N)[:, :, envs]
+    rb = rbar.cpu().numpy()[:, envs]
+    qb, qdb, ab = o.window_adjoint(qt.transpose(0, 2, 1), qdt.transpose(0, 2, 1), a.transpose(0, 2, 1), rb,
+                                   np.zeros((len(envs), model.nq)), np.zeros((len(envs), model.nv)))
+    g_a = outa[2].cpu().numpy().reshape(H, model.na, N)[:, :, envs].transpose(2, 0, 1).reshape(len(envs), -1)
+    g_q = outa[0].cpu().numpy().reshape(model.nq, N)[:, envs].T
+    g_qd = outa[1].cpu().numpy().reshape(model.nv, N)[:, envs].T
+    got = np.concatenate([g_a, g_q, g_qd], axis=1)
+    ref = np.concatenate([ab.transpose(1, 0, 2).reshape(len(envs), -1), qb, qdb], axis=1)
+    rel = np.linalg.norm(got - ref, axis=1) / np.linalg.norm(ref, axis=1)
+    return float(rel.max())
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_mod
+        backend = "gloo" if args.impl == "reference" else "nccl"
+        if backend == "nccl":
+            import torch
+            torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        dist_mod.init_process_group(backend)
+        dist = dist_mod
+    try:
+        if args.impl == "reference":
+            reference_main(args, rank, world)
+        else:
+            gpu_main(args, rank, world, dist)
+    finally:
+        if dist is not None:
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -473,6 +473,7 @@ __device__ void st_crba(const DevModel& M, const Mem& w, int lane, int nl) {
   const int n = M.nv;
   for (int a = lane; a < n; a += nl) {
     const int i = __ldg(M.dof_link + a);
+    for (int b = 0; b < a; ++b) w[M.o_M + a * n + b] = 0.f;   // zero unless b is an ancestor DOF
     V3 fn, ff;
     si_mul(w, M.o_IC + 10 * i, ld3(w, M.o_S + 6 * a), ld3(w, M.o_S + 6 * a + 3), fn, ff);
     for (int j = i; j >= 0; j = __ldg(M.parent + j)) {

@@ -12,9 +12,10 @@ GRAD_RTOL = 1e-3
 def assert_state_close(got, ref, what, rtol=STATE_RTOL, atol=STATE_ATOL):
     got = np.asarray(got, np.float64)
     ref = np.asarray(ref, np.float64)
+    assert np.isfinite(ref).all(), f"{what}: reference not finite"
     err = np.abs(got - ref)
     bound = atol + rtol * np.abs(ref)
-    bad = err > bound
+    bad = ~(err <= bound)          # NaN counts as a mismatch
     if bad.any():
         idx = np.argwhere(bad)[:5]
         raise AssertionError(f"{what}: {bad.sum()} / {bad.size} elements outside |d| <= {atol} + {rtol}|ref|; "
@@ -26,9 +27,10 @@ def assert_grad_close(got, ref, what, rtol=GRAD_RTOL, axis_env=-1):
     """Norm-wise per environment: |g - g*|_2 <= rtol |g*|_2 (env on the last axis)."""
     got = np.moveaxis(np.asarray(got, np.float64), axis_env, 0).reshape(np.shape(got)[axis_env], -1)
     ref = np.moveaxis(np.asarray(ref, np.float64), axis_env, 0).reshape(np.shape(ref)[axis_env], -1)
+    assert np.isfinite(ref).all(), f"{what}: reference not finite"
     num = np.linalg.norm(got - ref, axis=1)
     den = np.linalg.norm(ref, axis=1)
-    bad = num > rtol * np.maximum(den, 1e-30)
+    bad = ~(num <= rtol * np.maximum(den, 1e-30))   # NaN counts as a mismatch
     if bad.any():
         e = np.argwhere(bad)[:5].ravel()
         raise AssertionError(f"{what}: {bad.sum()} / {bad.size} envs outside rel {rtol}; envs {e.tolist()} "

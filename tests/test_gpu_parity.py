@@ -150,6 +150,7 @@ def test_plain_and_batched_agree_and_graph_replay_is_bitwise(oracle_mod):
     b = sb.window_forward(T(q0), T(qd0), act)
     torch.cuda.synchronize()
     for x, y in zip(a, b):
+        assert torch.isfinite(x).all() and torch.isfinite(y).all()
         np.testing.assert_allclose(x.cpu().numpy(), y.cpu().numpy(), rtol=1e-4, atol=1e-4)
     # CUDA-graph capture of the batched forward + adjoint window, replayed
     q0t, qd0t = T(q0), T(qd0)

@@ -73,8 +73,9 @@ static void compute_layout(shac_model* m) {
   auto take = [&](int& off, int n) { off = o; o += n; };
   take(d.o_Q, m->nq); take(d.o_QD, nv); take(d.o_ACT, m->na);
   take(d.o_QB, m->nq); take(d.o_QDB, nv); take(d.o_ACTB, m->na);
-  take(d.o_R, 9 * L); take(d.o_P, 3 * L); take(d.o_SI, 10 * L); take(d.o_S, 6 * nv); take(d.o_V, 6 * L);
-  take(d.o_A, 6 * L); take(d.o_F, 6 * L); take(d.o_FX, 6 * L); take(d.o_IT, 6 * ni); take(d.o_IC, 10 * L);
+  take(d.o_R, 9 * L); take(d.o_P, 3 * L); take(d.o_HZ, m->nc > 0 ? 8 * L : 0); take(d.o_SI, 10 * L);
+  take(d.o_S, 6 * nv); take(d.o_V, 6 * L);
+  take(d.o_A, 6 * L); take(d.o_F, 6 * L); take(d.o_FX, 6 * L); take(d.o_IT, 7 * ni); take(d.o_IC, 10 * L);
   take(d.o_M, nv * nv); take(d.o_LD, nv); take(d.o_B, nv); take(d.o_T, nv); take(d.o_QDD, nv);
   take(d.o_LAM, nv); take(d.o_SB, 6 * nv); take(d.o_VB, 6 * L); take(d.o_AB, 6 * L); take(d.o_FB, 6 * L);
   take(d.o_SIB, 12 * L); take(d.o_RB, 9 * L); take(d.o_PB, 3 * L); take(d.o_ITB, 9 * ni); take(d.o_TP, 12 * L);
@@ -284,15 +285,6 @@ static int default_lanes(const shac_model* m) {
 
 static int env_stride(const shac_model* m) { return ((m->layout.env_floats + 31) / 32) * 32 + 1; }
 
-static size_t batched_smem_bytes(const shac_batch* b) {
-  size_t per_warp = 0;
-  for (const Group& g : b->groups) {
-    if (g.N == 0) continue;
-    per_warp = std::max(per_warp, (size_t)(32 / g.lanes) * env_stride(g.m));
-  }
-  return per_warp * sizeof(float) * b->warps_per_cta;
-}
-
 static size_t batched_smem_warp_floats(const shac_batch* b) {
   size_t per_warp = 0;
   for (const Group& g : b->groups) {
@@ -300,6 +292,19 @@ static size_t batched_smem_warp_floats(const shac_batch* b) {
     per_warp = std::max(per_warp, (size_t)(32 / g.lanes) * env_stride(g.m));
   }
   return per_warp;
+}
+
+// Dynamic shared memory available to one CTA (227 KB per block on sm_103,
+// minus the kernels' static shared memory and a margin).
+constexpr size_t SMEM_BLOCK_LIMIT = 227 * 1024 - 8 * 1024;
+
+// Warps per CTA actually launched: the requested count, reduced until the
+// per-warp scratch fits in one CTA's shared memory (0 if one warp does not fit).
+static int batched_warps(const shac_batch* b) {
+  const size_t per_warp = batched_smem_warp_floats(b) * sizeof(float);
+  int W = b->warps_per_cta;
+  while (W > 0 && (size_t)W * per_warp > SMEM_BLOCK_LIMIT) --W;
+  return W;
 }
 
 // Work items sorted by per-warp cost (largest first) so the dynamic schedule
@@ -433,7 +438,7 @@ extern "C" shac_status shac_batch_set_launch(shac_batch* b, int32_t group, int32
 extern "C" shac_status shac_batch_get_launch(const shac_batch* b, int32_t group, int32_t* lanes, int32_t* warps) {
   if (!b || group < 0 || group >= (int)b->groups.size()) return SHAC_ERR_INVALID_ARG;
   if (lanes) *lanes = b->groups[group].lanes;
-  if (warps) *warps = b->warps_per_cta;
+  if (warps) *warps = b->form == SHAC_FORM_BATCHED ? batched_warps(b) : b->warps_per_cta;
   return SHAC_OK;
 }
 
@@ -464,14 +469,15 @@ static shac_status batched_launch(shac_batch* b, BatchedArgs& a, void* ws, cudaS
   for (int gi = 0; gi < a.n_groups; ++gi) a.tape_off[gi] = (int64_t)(b->batched_tape_off[gi] / sizeof(float));
   a.flags = b->d_flags;
   if (b->n_items == 0) return SHAC_OK;
-  const size_t smem = batched_smem_bytes(b);
-  const int block = 32 * b->warps_per_cta;
+  const int W = batched_warps(b);
+  if (W < 1) return SHAC_ERR_CAPACITY;
+  const size_t smem = (size_t)W * a.smem_warp_floats * sizeof(float);
+  const int block = 32 * W;
   if (smem > 48 * 1024 && batched_set_smem_limit(smem) != cudaSuccess) return SHAC_ERR_CAPACITY;
   int occ = 0;
   if (batched_occupancy(&occ, block, smem, adjoint) != cudaSuccess) return SHAC_ERR_CUDA;
   if (occ < 1) return SHAC_ERR_CAPACITY;
-  const int warps_needed = b->n_items;
-  const int grid = std::max(1, std::min(b->num_sms * occ, (warps_needed + b->warps_per_cta - 1) / b->warps_per_cta));
+  const int grid = std::max(1, std::min(b->num_sms * occ, (b->n_items + W - 1) / W));
   if (cudaMemsetAsync(a.counter, 0, sizeof(int), s) != cudaSuccess) return SHAC_ERR_CUDA;
   if (adjoint) launch_batched_adjoint(a, grid, block, smem, s);
   else launch_batched_forward(a, grid, block, smem, s);

@@ -69,7 +69,7 @@ struct DevModel {
   const float *rwq, *rwqd;
   // per-environment scratch layout (float offsets)
   int o_Q, o_QD, o_ACT, o_QB, o_QDB, o_ACTB;
-  int o_R, o_P, o_SI, o_S, o_V, o_A, o_F, o_FX, o_IT, o_IC, o_M, o_LD, o_B, o_T, o_QDD;
+  int o_R, o_P, o_HZ, o_SI, o_S, o_V, o_A, o_F, o_FX, o_IT, o_IC, o_M, o_LD, o_B, o_T, o_QDD;
   int o_LAM, o_SB, o_VB, o_AB, o_FB, o_SIB, o_RB, o_PB, o_ITB, o_TP, o_SEGA;
   int env_floats;
 };
@@ -194,6 +194,59 @@ __device__ __forceinline__ void si_mul(const Mem& w, int o, V3 xw, V3 xv, V3& yn
   yf = m * xv - cross(h, xw);
 }
 
+// A double kept in two float slots (hi + lo, 48-bit significand).
+template <class Mem> __device__ __forceinline__ void st_d(const Mem& w, int o, double v) {
+  const float hi = (float)v;
+  w[o] = hi;
+  w[o + 1] = (float)(v - (double)hi);
+}
+template <class Mem> __device__ __forceinline__ double ld_d(const Mem& w, int o) {
+  return (double)w[o] + (double)w[o + 1];
+}
+
+// Height chain in FP64 (models with contacts): the third row of each link
+// rotation and the link origin height.  Contact penetration depths of a few
+// millimetres sit under ~1 m of kinematic chain; in FP32 their rounding error
+// (~1e-7 m) would reach 1e-4 of the penalty force, so depths come from here.
+template <class Mem>
+__device__ __forceinline__ void fk_height(const DevModel& M, const Mem& w, int i, int jt, int s, int p) {
+  double r0, r1, r2, pz;
+  if (jt == J_FREE) {
+    const double x = w[M.o_Q + s + 3], y = w[M.o_Q + s + 4], z = w[M.o_Q + s + 5], qw = w[M.o_Q + s + 6];
+    r0 = 2.0 * (x * z - y * qw); r1 = 2.0 * (y * z + x * qw); r2 = 1.0 - 2.0 * (x * x + y * y);
+    pz = w[M.o_Q + s + 2];
+  } else {
+    double a0 = 0.0, a1 = 0.0, a2 = 1.0, pp = 0.0;
+    if (p >= 0) {
+      const int o = M.o_HZ + 8 * p;
+      a0 = ld_d(w, o); a1 = ld_d(w, o + 2); a2 = ld_d(w, o + 4); pp = ld_d(w, o + 6);
+    }
+    const float* J = M.jrot + 9 * i;
+    const float* jp = M.jpos + 3 * i;
+    // row of Rj = (row of Rp) * jrot ; Pj.z = Pp.z + (row of Rp) . jpos
+    const double b0 = a0 * __ldg(J) + a1 * __ldg(J + 3) + a2 * __ldg(J + 6);
+    const double b1 = a0 * __ldg(J + 1) + a1 * __ldg(J + 4) + a2 * __ldg(J + 7);
+    const double b2 = a0 * __ldg(J + 2) + a1 * __ldg(J + 5) + a2 * __ldg(J + 8);
+    pz = pp + a0 * __ldg(jp) + a1 * __ldg(jp + 1) + a2 * __ldg(jp + 2);
+    const double ax = __ldg(M.axis + 3 * i), ay = __ldg(M.axis + 3 * i + 1), az = __ldg(M.axis + 3 * i + 2);
+    const double q = w[M.o_Q + s];
+    if (jt == J_REV) {
+      double sn, c;
+      sincos(q, &sn, &c);
+      const double k = 1.0 - c;
+      // row * Rot(axis, q)
+      r0 = b0 * (c + k * ax * ax) + b1 * (k * ay * ax + sn * az) + b2 * (k * az * ax - sn * ay);
+      r1 = b0 * (k * ax * ay - sn * az) + b1 * (c + k * ay * ay) + b2 * (k * az * ay + sn * ax);
+      r2 = b0 * (k * ax * az + sn * ay) + b1 * (k * ay * az - sn * ax) + b2 * (c + k * az * az);
+    } else {
+      r0 = b0; r1 = b1; r2 = b2;
+      if (jt == J_PRIS) pz += (b0 * ax + b1 * ay + b2 * az) * q;
+    }
+  }
+  const int o = M.o_HZ + 8 * i;
+  st_d(w, o, r0); st_d(w, o + 2, r1); st_d(w, o + 4, r2); st_d(w, o + 6, pz);
+}
+
 // ================================================================= FORWARD ==
 
 // Forward kinematics, level by level: link rotation R_i and origin P_i (world).
@@ -229,6 +282,7 @@ __device__ void st_fk(const DevModel& M, const Mem& w, int lane, int nl) {
       }
       stm(w, M.o_R + 9 * i, R);
       st3(w, M.o_P + 3 * i, P);
+      if (M.nc > 0) fk_height(M, w, i, jt, s, p);
     }
     team_sync(nl);
   }
@@ -316,12 +370,16 @@ __device__ void st_items(const DevModel& M, const Mem& w, int lane, int nl) {
   for (int c = lane; c < M.nc; c += nl) {
     const int i = __ldg(M.item_link + c);
     M33 R = ldm(w, M.o_R + 9 * i);
-    V3 x = ld3(w, M.o_P + 3 * i) + mul(R, cld3(M.item_pos + 3 * c));
+    const V3 lp = cld3(M.item_pos + 3 * c);
+    V3 x = ld3(w, M.o_P + 3 * i) + mul(R, lp);
     x.z -= __ldg(M.crad + c);
+    const int oh = M.o_HZ + 8 * i;
+    const float d = (float)(ld_d(w, oh + 6) + ld_d(w, oh) * lp.x + ld_d(w, oh + 2) * lp.y + ld_d(w, oh + 4) * lp.z -
+                            (double)__ldg(M.crad + c));
     V3 f = v3(0.f, 0.f, 0.f);
-    if (x.z < 0.f) {
+    if (d < 0.f) {
       V3 vp = ld3(w, M.o_V + 6 * i + 3) + cross(ld3(w, M.o_V + 6 * i), x);
-      float fn = (-M.ke + M.kd * vp.z) * x.z;
+      float fn = (-M.ke + M.kd * vp.z) * d;
       float vt2 = vp.x * vp.x + vp.y * vp.y;
       float vt = sqrtf(vt2);
       float afn = fabsf(fn);
@@ -329,8 +387,9 @@ __device__ void st_items(const DevModel& M, const Mem& w, int lane, int nl) {
       else { float s = M.mu * afn / vt; f.x = -s * vp.x; f.y = -s * vp.y; }
       f.z = fn;
     }
-    st3(w, M.o_IT + 6 * c, x);
-    st3(w, M.o_IT + 6 * c + 3, f);
+    st3(w, M.o_IT + 7 * c, x);
+    st3(w, M.o_IT + 7 * c + 3, f);
+    w[M.o_IT + 7 * c + 6] = d;
   }
   for (int sg = lane; sg < M.nseg; sg += nl) {
     const int e0 = M.nc + 2 * sg, e1 = e0 + 1;
@@ -343,17 +402,17 @@ __device__ void st_items(const DevModel& M, const Mem& w, int lane, int nl) {
     V3 dv = x1 - x0;
     float inv = 1.f / sqrtf(dot(dv, dv));
     V3 u = inv * dv;
-    st3(w, M.o_IT + 6 * e0, x0);
-    st3(w, M.o_IT + 6 * e0 + 3, F * u);
-    st3(w, M.o_IT + 6 * e1, x1);
-    st3(w, M.o_IT + 6 * e1 + 3, -F * u);
+    st3(w, M.o_IT + 7 * e0, x0);
+    st3(w, M.o_IT + 7 * e0 + 3, F * u);
+    st3(w, M.o_IT + 7 * e1, x1);
+    st3(w, M.o_IT + 7 * e1 + 3, -F * u);
   }
   team_sync(nl);
   for (int i = lane; i < M.L; i += nl) {
     V3 n = v3(0.f, 0.f, 0.f), f = v3(0.f, 0.f, 0.f);
     for (int k = __ldg(M.li_ptr + i); k < __ldg(M.li_ptr + i + 1); ++k) {
       const int e = __ldg(M.li_idx + k);
-      V3 x = ld3(w, M.o_IT + 6 * e), fe = ld3(w, M.o_IT + 6 * e + 3);
+      V3 x = ld3(w, M.o_IT + 7 * e), fe = ld3(w, M.o_IT + 7 * e + 3);
       n = n + cross(x, fe);
       f = f + fe;
     }
@@ -796,9 +855,10 @@ __device__ void st_dynamics_adj(const DevModel& M, const Mem& w, int lane, int n
   // force items (external wrench Fext_i enters F_i with a minus sign)
   for (int c = lane; c < M.nc; c += nl) {
     const int i = __ldg(M.item_link + c);
-    V3 x = ld3(w, M.o_IT + 6 * c), f = ld3(w, M.o_IT + 6 * c + 3);
+    V3 x = ld3(w, M.o_IT + 7 * c), f = ld3(w, M.o_IT + 7 * c + 3);
+    const float dep = w[M.o_IT + 7 * c + 6];
     V3 xb = v3(0.f, 0.f, 0.f), wb = v3(0.f, 0.f, 0.f), vob = v3(0.f, 0.f, 0.f);
-    if (x.z < 0.f) {
+    if (dep < 0.f) {
       V3 neb = -ld3(w, M.o_FB + 6 * i), feb = -ld3(w, M.o_FB + 6 * i + 3);
       V3 fbar = cross(neb, x) + feb;
       xb = cross(f, neb);
@@ -823,8 +883,8 @@ __device__ void st_dynamics_adj(const DevModel& M, const Mem& w, int lane, int n
         vpb.y += vtb * vp.y / vt;
       }
       // fn = (-ke + kd ddot) d
-      xb.z += fnb * (-M.ke + M.kd * vp.z);
-      vpb.z += fnb * M.kd * x.z;
+      xb.z += fnb * (-M.ke + M.kd * vp.z);   // the depth is the height of x
+      vpb.z += fnb * M.kd * dep;
       vob = vpb;
       wb = cross(x, vpb);
       xb = xb + cross(vpb, Vw);
@@ -836,8 +896,8 @@ __device__ void st_dynamics_adj(const DevModel& M, const Mem& w, int lane, int n
   for (int sg = lane; sg < M.nseg; sg += nl) {
     const int e0 = M.nc + 2 * sg, e1 = e0 + 1;
     const int l0 = __ldg(M.item_link + e0), l1 = __ldg(M.item_link + e1);
-    V3 x0 = ld3(w, M.o_IT + 6 * e0), f0 = ld3(w, M.o_IT + 6 * e0 + 3);
-    V3 x1 = ld3(w, M.o_IT + 6 * e1), f1 = ld3(w, M.o_IT + 6 * e1 + 3);
+    V3 x0 = ld3(w, M.o_IT + 7 * e0), f0 = ld3(w, M.o_IT + 7 * e0 + 3);
+    V3 x1 = ld3(w, M.o_IT + 7 * e1), f1 = ld3(w, M.o_IT + 7 * e1 + 3);
     V3 n0b = -ld3(w, M.o_FB + 6 * l0), f0eb = -ld3(w, M.o_FB + 6 * l0 + 3);
     V3 n1b = -ld3(w, M.o_FB + 6 * l1), f1eb = -ld3(w, M.o_FB + 6 * l1 + 3);
     V3 f0b = cross(n0b, x0) + f0eb, f1b = cross(n1b, x1) + f1eb;

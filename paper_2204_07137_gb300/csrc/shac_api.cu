@@ -73,7 +73,7 @@ static void compute_layout(shac_model* m) {
   auto take = [&](int& off, int n) { off = o; o += n; };
   take(d.o_Q, m->nq); take(d.o_QD, nv); take(d.o_ACT, m->na);
   take(d.o_QB, m->nq); take(d.o_QDB, nv); take(d.o_ACTB, m->na);
-  take(d.o_R, 9 * L); take(d.o_P, 3 * L); take(d.o_HZ, m->nc > 0 ? 8 * L : 0); take(d.o_SI, 10 * L);
+  take(d.o_R, 9 * L); take(d.o_P, 3 * L); take(d.o_QC, m->nq); take(d.o_QDC, nv); take(d.o_SI, 10 * L);
   take(d.o_S, 6 * nv); take(d.o_V, 6 * L);
   take(d.o_A, 6 * L); take(d.o_F, 6 * L); take(d.o_FX, 6 * L); take(d.o_IT, 7 * ni); take(d.o_IC, 10 * L);
   take(d.o_M, nv * nv); take(d.o_LD, nv); take(d.o_B, nv); take(d.o_T, nv); take(d.o_QDD, nv);

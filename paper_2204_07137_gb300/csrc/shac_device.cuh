@@ -69,7 +69,8 @@ struct DevModel {
   const float *rwq, *rwqd;
   // per-environment scratch layout (float offsets)
   int o_Q, o_QD, o_ACT, o_QB, o_QDB, o_ACTB;
-  int o_R, o_P, o_HZ, o_SI, o_S, o_V, o_A, o_F, o_FX, o_IT, o_IC, o_M, o_LD, o_B, o_T, o_QDD;
+  int o_R, o_P, o_SI, o_S, o_V, o_A, o_F, o_FX, o_IT, o_IC, o_M, o_LD, o_B, o_T, o_QDD;
+  int o_QC, o_QDC;                       // compensation (low parts) of q, qd within a step
   int o_LAM, o_SB, o_VB, o_AB, o_FB, o_SIB, o_RB, o_PB, o_ITB, o_TP, o_SEGA;
   int env_floats;
 };
@@ -194,59 +195,6 @@ __device__ __forceinline__ void si_mul(const Mem& w, int o, V3 xw, V3 xv, V3& yn
   yf = m * xv - cross(h, xw);
 }
 
-// A double kept in two float slots (hi + lo, 48-bit significand).
-template <class Mem> __device__ __forceinline__ void st_d(const Mem& w, int o, double v) {
-  const float hi = (float)v;
-  w[o] = hi;
-  w[o + 1] = (float)(v - (double)hi);
-}
-template <class Mem> __device__ __forceinline__ double ld_d(const Mem& w, int o) {
-  return (double)w[o] + (double)w[o + 1];
-}
-
-// Height chain in FP64 (models with contacts): the third row of each link
-// rotation and the link origin height.  Contact penetration depths of a few
-// millimetres sit under ~1 m of kinematic chain; in FP32 their rounding error
-// (~1e-7 m) would reach 1e-4 of the penalty force, so depths come from here.
-template <class Mem>
-__device__ __forceinline__ void fk_height(const DevModel& M, const Mem& w, int i, int jt, int s, int p) {
-  double r0, r1, r2, pz;
-  if (jt == J_FREE) {
-    const double x = w[M.o_Q + s + 3], y = w[M.o_Q + s + 4], z = w[M.o_Q + s + 5], qw = w[M.o_Q + s + 6];
-    r0 = 2.0 * (x * z - y * qw); r1 = 2.0 * (y * z + x * qw); r2 = 1.0 - 2.0 * (x * x + y * y);
-    pz = w[M.o_Q + s + 2];
-  } else {
-    double a0 = 0.0, a1 = 0.0, a2 = 1.0, pp = 0.0;
-    if (p >= 0) {
-      const int o = M.o_HZ + 8 * p;
-      a0 = ld_d(w, o); a1 = ld_d(w, o + 2); a2 = ld_d(w, o + 4); pp = ld_d(w, o + 6);
-    }
-    const float* J = M.jrot + 9 * i;
-    const float* jp = M.jpos + 3 * i;
-    // row of Rj = (row of Rp) * jrot ; Pj.z = Pp.z + (row of Rp) . jpos
-    const double b0 = a0 * __ldg(J) + a1 * __ldg(J + 3) + a2 * __ldg(J + 6);
-    const double b1 = a0 * __ldg(J + 1) + a1 * __ldg(J + 4) + a2 * __ldg(J + 7);
-    const double b2 = a0 * __ldg(J + 2) + a1 * __ldg(J + 5) + a2 * __ldg(J + 8);
-    pz = pp + a0 * __ldg(jp) + a1 * __ldg(jp + 1) + a2 * __ldg(jp + 2);
-    const double ax = __ldg(M.axis + 3 * i), ay = __ldg(M.axis + 3 * i + 1), az = __ldg(M.axis + 3 * i + 2);
-    const double q = w[M.o_Q + s];
-    if (jt == J_REV) {
-      double sn, c;
-      sincos(q, &sn, &c);
-      const double k = 1.0 - c;
-      // row * Rot(axis, q)
-      r0 = b0 * (c + k * ax * ax) + b1 * (k * ay * ax + sn * az) + b2 * (k * az * ax - sn * ay);
-      r1 = b0 * (k * ax * ay - sn * az) + b1 * (c + k * ay * ay) + b2 * (k * az * ay + sn * ax);
-      r2 = b0 * (k * ax * az + sn * ay) + b1 * (k * ay * az - sn * ax) + b2 * (c + k * az * az);
-    } else {
-      r0 = b0; r1 = b1; r2 = b2;
-      if (jt == J_PRIS) pz += (b0 * ax + b1 * ay + b2 * az) * q;
-    }
-  }
-  const int o = M.o_HZ + 8 * i;
-  st_d(w, o, r0); st_d(w, o + 2, r1); st_d(w, o + 4, r2); st_d(w, o + 6, pz);
-}
-
 // ================================================================= FORWARD ==
 
 // Forward kinematics, level by level: link rotation R_i and origin P_i (world).
@@ -282,7 +230,6 @@ __device__ void st_fk(const DevModel& M, const Mem& w, int lane, int nl) {
       }
       stm(w, M.o_R + 9 * i, R);
       st3(w, M.o_P + 3 * i, P);
-      if (M.nc > 0) fk_height(M, w, i, jt, s, p);
     }
     team_sync(nl);
   }
@@ -373,9 +320,7 @@ __device__ void st_items(const DevModel& M, const Mem& w, int lane, int nl) {
     const V3 lp = cld3(M.item_pos + 3 * c);
     V3 x = ld3(w, M.o_P + 3 * i) + mul(R, lp);
     x.z -= __ldg(M.crad + c);
-    const int oh = M.o_HZ + 8 * i;
-    const float d = (float)(ld_d(w, oh + 6) + ld_d(w, oh) * lp.x + ld_d(w, oh + 2) * lp.y + ld_d(w, oh + 4) * lp.z -
-                            (double)__ldg(M.crad + c));
+    const float d = x.z;
     V3 f = v3(0.f, 0.f, 0.f);
     if (d < 0.f) {
       V3 vp = ld3(w, M.o_V + 6 * i + 3) + cross(ld3(w, M.o_V + 6 * i), x);
@@ -582,18 +527,38 @@ __device__ void st_solve(const DevModel& M, const Mem& w, int lane, int nl, int 
   }
 }
 
+// Exact sum of two floats: s + e == a + b (Knuth's two-sum).
+__device__ __forceinline__ float two_sum(float a, float b, float& e) {
+  const float s = a + b;
+  const float bp = s - a;
+  const float ap = s - bp;
+  e = (a - ap) + (b - bp);
+  return s;
+}
+
 // Semi-implicit Euler: qd += h qdd, then q += h qd (new velocity); free root:
 // p += h R v_b, quat <- normalise(quat + h/2 quat (x) (w_b, 0)).
+// The state stays FP32 between substeps; the rounding of each accumulation
+// is carried in o_QC/o_QDC (zeroed at every step start) and fed back into the
+// next substep's update, so a step of K substeps rounds its state once.
 template <class Mem>
 __device__ void st_integrate(const DevModel& M, const Mem& w, int lane, int nl) {
-  for (int d = lane; d < M.nv; d += nl) w[M.o_QD + d] += M.h * w[M.o_QDD + d];
+  for (int d = lane; d < M.nv; d += nl) {
+    float e;
+    const float y = M.h * w[M.o_QDD + d] + w[M.o_QDC + d];
+    w[M.o_QD + d] = two_sum(w[M.o_QD + d], y, e);
+    w[M.o_QDC + d] = e;
+  }
   team_sync(nl);
   for (int i = lane; i < M.L; i += nl) {
     const int jt = __ldg(M.jtype + i), s = __ldg(M.qs + i), d = __ldg(M.ds + i);
     if (jt == J_FREE) {
       M33 R = ldm(w, M.o_R + 9 * i);
-      V3 vb = ld3(w, M.o_QD + d + 3);
-      add3(w, M.o_Q + s, M.h * mul(R, vb));
+      V3 dp = M.h * mul(R, ld3(w, M.o_QD + d + 3)) + M.h * mul(R, ld3(w, M.o_QDC + d + 3));
+      float e;
+      w[M.o_Q + s] = two_sum(w[M.o_Q + s], dp.x + w[M.o_QC + s], e); w[M.o_QC + s] = e;
+      w[M.o_Q + s + 1] = two_sum(w[M.o_Q + s + 1], dp.y + w[M.o_QC + s + 1], e); w[M.o_QC + s + 1] = e;
+      w[M.o_Q + s + 2] = two_sum(w[M.o_Q + s + 2], dp.z + w[M.o_QC + s + 2], e); w[M.o_QC + s + 2] = e;
       float x = w[M.o_Q + s + 3], y = w[M.o_Q + s + 4], z = w[M.o_Q + s + 5], qw = w[M.o_Q + s + 6];
       V3 om = ld3(w, M.o_QD + d);
       V3 u = v3(x, y, z);
@@ -604,10 +569,20 @@ __device__ void st_integrate(const DevModel& M, const Mem& w, int lane, int nl) 
       float inv = rsqrtf(nx * nx + ny * ny + nz * nz + nw * nw);
       w[M.o_Q + s + 3] = nx * inv; w[M.o_Q + s + 4] = ny * inv; w[M.o_Q + s + 5] = nz * inv; w[M.o_Q + s + 6] = nw * inv;
     } else if (jt == J_REV || jt == J_PRIS) {
-      w[M.o_Q + s] += M.h * w[M.o_QD + d];
+      float e;
+      const float y = M.h * w[M.o_QD + d] + (M.h * w[M.o_QDC + d] + w[M.o_QC + s]);
+      w[M.o_Q + s] = two_sum(w[M.o_Q + s], y, e);
+      w[M.o_QC + s] = e;
     }
   }
   team_sync(nl);
+}
+
+// Clear the integration compensation at a step start (team-parallel).
+template <class Mem>
+__device__ __forceinline__ void clear_comp(const DevModel& M, const Mem& w, int lane, int nl) {
+  for (int j = lane; j < M.nq; j += nl) w[M.o_QC + j] = 0.f;
+  for (int j = lane; j < M.nv; j += nl) w[M.o_QDC + j] = 0.f;
 }
 
 // One forward substep (everything up to and including the integration).

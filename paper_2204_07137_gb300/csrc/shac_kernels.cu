@@ -56,7 +56,10 @@ __global__ void k_plain_load(PlainGroup g, const float* __restrict__ q, const fl
   GMem w{g.ws + e, g.N};
   if (q) for (int j = 0; j < M.nq; ++j) w[M.o_Q + j] = q[(size_t)j * g.N + e];
   if (qd) for (int j = 0; j < M.nv; ++j) w[M.o_QD + j] = qd[(size_t)j * g.N + e];
-  if (act) for (int j = 0; j < M.na; ++j) w[M.o_ACT + j] = act[(size_t)j * g.N + e];
+  if (act) {   // every step starts by loading its action: clear the integration compensation
+    for (int j = 0; j < M.na; ++j) w[M.o_ACT + j] = act[(size_t)j * g.N + e];
+    clear_comp(M, w, 0, 1);
+  }
 }
 
 __global__ void k_plain_store(PlainGroup g, float* __restrict__ q, float* __restrict__ qd, float* __restrict__ rew,
@@ -212,6 +215,7 @@ __global__ void __launch_bounds__(BATCHED_BLOCK_MAX) k_batched_forward(BatchedAr
     }
     for (int step = 0; step < a.h; ++step) {
       team_load(w, M.o_ACT, a.act + (size_t)step * a.io.act_size + io.act_off, M.na, io.N, t.env, t.lane, t.nl);
+      clear_comp(M, w, t.lane, t.nl);
       team_sync(t.nl);
       for (int k = 0; k < M.K; ++k) {
         substep_dynamics(M, w, t.lane, t.nl);
@@ -254,6 +258,7 @@ __global__ void __launch_bounds__(BATCHED_BLOCK_MAX) k_batched_adjoint(BatchedAr
       team_load(w, M.o_QD, a.qd_traj + (size_t)step * a.io.qd_size + io.qd_off, M.nv, io.N, t.env, t.lane, t.nl);
       team_load(w, M.o_ACT, a.act + (size_t)step * a.io.act_size + io.act_off, M.na, io.N, t.env, t.lane, t.nl);
       zero_range(w, M.o_ACTB, M.na, t.lane, t.nl);
+      clear_comp(M, w, t.lane, t.nl);
       team_sync(t.nl);
       // recompute the substeps, keeping each substep's start state
       for (int k = 0; k < M.K; ++k) {

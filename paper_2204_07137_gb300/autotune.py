@@ -21,22 +21,6 @@ from .sim import Simulator
 
 LANES = (1, 2, 4, 8, 16, 32)
 WARPS = (1, 2, 4, 8)
-SMEM_LIMIT = 227 * 1024 - 8 * 1024
-
-
-def _env_floats(sim: Simulator, g: int) -> int:
-    # per-environment scratch floats (same layout arithmetic as the library)
-    m = sim.groups[g][0]
-    L, nv, nq, na = m.n_links, m.nv, m.nq, m.na
-    nseg = int(sum(int(m.muscle_ptr[k + 1] - m.muscle_ptr[k] - 1) for k in range(m.n_muscles)))
-    ni = m.n_contacts + 2 * nseg
-    return (2 * (nq + nv + na) + 9 * L + 3 * L + nq + nv + 10 * L + 6 * nv + 24 * L + 7 * ni + 10 * L + nv * nv
-            + 6 * nv + 6 * nv + 18 * L + 12 * L + 9 * L + 3 * L + 9 * ni + 12 * L + nseg)
-
-
-def _fits(sim: Simulator, g: int, lanes: int) -> bool:
-    stride = (_env_floats(sim, g) + 31) // 32 * 32 + 1
-    return (32 // lanes) * stride * 4 <= SMEM_LIMIT
 
 
 class _Inputs:
@@ -83,7 +67,7 @@ def autotune(sim: Simulator, h: int = 4, reps: int = 3, verbose: bool = False) -
             sim.set_launch(g, l, w)
 
     def measure(ls, w):
-        try:
+        try:   # shapes whose scratch does not fit in shared memory are rejected by the library
             apply(ls, w)
             t = time_window(sim, x, reps)
         except _lib.ShacError:
@@ -96,7 +80,7 @@ def autotune(sim: Simulator, h: int = 4, reps: int = 3, verbose: bool = False) -
     best = measure(lanes, warps)
     for g in range(len(sim.groups)):
         for l in LANES:
-            if l == lanes[g] or not _fits(sim, g, l):
+            if l == lanes[g]:
                 continue
             trial = list(lanes)
             trial[g] = l

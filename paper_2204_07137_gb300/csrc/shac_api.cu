@@ -15,7 +15,7 @@ struct shac_model {
   float h = 0, grav[3] = {0, 0, 0}, ke = 0, kd = 0, kt = 0, mu = 0, klim = 0, rc[10] = {0};
   int root_free = 0;
   std::vector<int> parent, jtype, qs, ds, nd, lvl_ptr, lvl_link, ch_ptr, ch_idx, li_ptr, li_idx, dof_link, dof_k,
-      dof_act, item_link, seg_mus, mus_seg_ptr;
+      dof_act, item_link, seg_mus, mus_seg_ptr, anc_mask;
   std::vector<float> axis, jpos, jrot, mass, com, icom, qlo, qhi, arm, damp, gear, item_pos, crad, fmax, rwq, rwqd;
   DevModel layout;   // sizes + scratch offsets (pointers unset)
 };
@@ -78,7 +78,7 @@ static void compute_layout(shac_model* m) {
   take(d.o_A, 6 * L); take(d.o_F, 6 * L); take(d.o_FX, 6 * L); take(d.o_IT, 7 * ni); take(d.o_IC, 10 * L);
   take(d.o_M, nv * nv); take(d.o_LD, nv); take(d.o_B, nv); take(d.o_T, nv); take(d.o_QDD, nv);
   take(d.o_LAM, nv); take(d.o_SB, 6 * nv); take(d.o_VB, 6 * L); take(d.o_AB, 6 * L); take(d.o_FB, 6 * L);
-  take(d.o_SIB, 12 * L); take(d.o_RB, 9 * L); take(d.o_PB, 3 * L); take(d.o_ITB, 9 * ni); take(d.o_TP, 12 * L);
+  take(d.o_SIB, 12 * L); take(d.o_RB, 9 * L); take(d.o_PB, 3 * L); take(d.o_ITB, 10 * ni); take(d.o_TP, 12 * L);
   take(d.o_SEGA, m->nseg);
   d.env_floats = o;
 }
@@ -151,6 +151,13 @@ extern "C" shac_status shac_model_create(const shac_model_desc* dsc, shac_model*
   // dofs
   for (int i = 0; i < L; ++i)
     for (int k = 0; k < m->nd[i]; ++k) { m->dof_link.push_back(i); m->dof_k.push_back(k); }
+  for (int a = 0; a < nv; ++a) {
+    unsigned mask = 0u;
+    for (int j = m->dof_link[a]; j >= 0; j = m->parent[j])
+      for (int b = m->ds[j]; b < m->ds[j] + m->nd[j]; ++b)
+        if (b <= a) mask |= 1u << b;
+    m->anc_mask.push_back((int)mask);
+  }
   if (!dsc->q_lower || !dsc->q_upper || !dsc->armature || !dsc->joint_damping) { delete m; return SHAC_ERR_INVALID_ARG; }
   m->qlo.assign(dsc->q_lower, dsc->q_lower + nv);
   m->qhi.assign(dsc->q_upper, dsc->q_upper + nv);
@@ -256,6 +263,11 @@ static shac_status upload_model(const shac_model* m, Group& g) {
   addi(&d.li_ptr, m->li_ptr); addi(&d.li_idx, m->li_idx); addi(&d.dof_link, m->dof_link); addi(&d.dof_k, m->dof_k);
   addi(&d.dof_act, m->dof_act); addi(&d.item_link, m->item_link); addi(&d.seg_mus, m->seg_mus);
   addi(&d.mus_seg_ptr, m->mus_seg_ptr);
+  {
+    const int* tmp = nullptr;
+    addi(&tmp, m->anc_mask);
+    ifix.back().first = reinterpret_cast<const int**>(&d.anc_mask);
+  }
   addf(&d.axis, m->axis); addf(&d.jpos, m->jpos); addf(&d.jrot, m->jrot); addf(&d.mass, m->mass); addf(&d.com, m->com);
   addf(&d.icom, m->icom); addf(&d.qlo, m->qlo); addf(&d.qhi, m->qhi); addf(&d.arm, m->arm); addf(&d.damp, m->damp);
   addf(&d.gear, m->gear); addf(&d.item_pos, m->item_pos); addf(&d.crad, m->crad); addf(&d.fmax, m->fmax);
@@ -280,6 +292,15 @@ static int default_lanes(const shac_model* m) {
   if (par <= 4) return 4;
   if (par <= 8) return 8;
   if (par <= 16) return 16;
+  return 32;
+}
+
+// Register row capacity of the batched dense path: a team needs one lane per
+// DOF; 0 selects the shared-memory form.
+static int dense_class(int nv, int lanes) {
+  if (lanes < nv) return 0;
+  if (nv <= 8) return 8;
+  if (nv <= 16) return 16;
   return 32;
 }
 
@@ -426,7 +447,7 @@ extern "C" shac_status shac_batch_set_launch(shac_batch* b, int32_t group, int32
   if (!b || group < -1 || group >= (int)b->groups.size()) return SHAC_ERR_INVALID_ARG;
   if (lanes != 0 && lanes != 1 && lanes != 2 && lanes != 4 && lanes != 8 && lanes != 16 && lanes != 32)
     return SHAC_ERR_INVALID_ARG;
-  if (warps < 0 || warps > 16) return SHAC_ERR_INVALID_ARG;
+  if (warps < 0 || warps > 8) return SHAC_ERR_INVALID_ARG;
   for (int gi = 0; gi < (int)b->groups.size(); ++gi) {
     if (group >= 0 && gi != group) continue;
     b->groups[gi].lanes = lanes == 0 ? default_lanes(b->groups[gi].m) : lanes;
@@ -460,6 +481,7 @@ static shac_status batched_launch(shac_batch* b, BatchedArgs& a, void* ws, cudaS
   for (int gi = 0; gi < a.n_groups; ++gi) {
     a.lanes[gi] = b->groups[gi].lanes;
     a.env_stride[gi] = env_stride(b->groups[gi].m);
+    a.dense_nm[gi] = dense_class(b->groups[gi].m->nv, b->groups[gi].lanes);
   }
   a.smem_warp_floats = (int)batched_smem_warp_floats(b);
   a.items = b->d_items;

@@ -59,6 +59,7 @@ struct DevModel {
   const float *axis, *jpos, *jrot, *mass, *com, *icom;
   // dofs
   const int *dof_link, *dof_k, *dof_act;
+  const unsigned *anc_mask;              // per DOF a: bit b set when DOF b <= a moves an ancestor-or-self link of a
   const float *qlo, *qhi, *arm, *damp, *gear;
   // force items: contacts [0, nc) then muscle segment ends [nc, nc + 2 nseg)
   const int *item_link;
@@ -207,8 +208,10 @@ __device__ void st_fk(const DevModel& M, const Mem& w, int lane, int nl) {
       M33 R;
       V3 P;
       if (jt == J_FREE) {
+        // Spatial quantities use the free root's origin as reference point
+        // (translation invariance); only contact depths need its height back.
         R = quat_to_R(w[M.o_Q + s + 3], w[M.o_Q + s + 4], w[M.o_Q + s + 5], w[M.o_Q + s + 6]);
-        P = ld3(w, M.o_Q + s);
+        P = v3(0.f, 0.f, 0.f);
       } else {
         M33 Rj = cldm(M.jrot + 9 * i);
         V3 Pj = cld3(M.jpos + 3 * i);
@@ -320,7 +323,7 @@ __device__ void st_items(const DevModel& M, const Mem& w, int lane, int nl) {
     const V3 lp = cld3(M.item_pos + 3 * c);
     V3 x = ld3(w, M.o_P + 3 * i) + mul(R, lp);
     x.z -= __ldg(M.crad + c);
-    const float d = x.z;
+    const float d = x.z + (M.root_free ? w[M.o_Q + 2] : 0.f);   // height above the plane
     V3 f = v3(0.f, 0.f, 0.f);
     if (d < 0.f) {
       V3 vp = ld3(w, M.o_V + 6 * i + 3) + cross(ld3(w, M.o_V + 6 * i), x);
@@ -454,10 +457,10 @@ __device__ void st_rhs(const DevModel& M, const Mem& w, int lane, int nl) {
   team_sync(nl);
 }
 
-// CRBA: composite inertias (gather, leaves first), then the lower triangle of
-// M row by row (row a owns M[a][b], b <= a), armature on the diagonal.
+// CRBA part 1: composite spatial inertias Ic_i = I_i + sum_children Ic_c
+// (gather, leaves first).
 template <class Mem>
-__device__ void st_crba(const DevModel& M, const Mem& w, int lane, int nl) {
+__device__ void st_composite(const DevModel& M, const Mem& w, int lane, int nl) {
   for (int l = M.nlev - 1; l >= 0; --l) {
     for (int ii = __ldg(M.lvl_ptr + l) + lane; ii < __ldg(M.lvl_ptr + l + 1); ii += nl) {
       const int i = __ldg(M.lvl_link + ii);
@@ -474,6 +477,12 @@ __device__ void st_crba(const DevModel& M, const Mem& w, int lane, int nl) {
     }
     team_sync(nl);
   }
+}
+
+// Lower triangle of M row by row (row a owns M[a][b], b <= a), armature on
+// the diagonal (shared-memory form).
+template <class Mem>
+__device__ void st_mass_rows(const DevModel& M, const Mem& w, int lane, int nl) {
   const int n = M.nv;
   for (int a = lane; a < n; a += nl) {
     const int i = __ldg(M.dof_link + a);
@@ -585,8 +594,87 @@ __device__ __forceinline__ void clear_comp(const DevModel& M, const Mem& w, int 
   for (int j = lane; j < M.nv; j += nl) w[M.o_QDC + j] = 0.f;
 }
 
-// One forward substep (everything up to and including the integration).
+// ---- register-resident dense path (teams with at least nv lanes) ----------
+// Lane a of the team owns row a of M.  The row is assembled in registers
+// (CRBA part 2), factorised by a right-looking Cholesky whose column k is
+// broadcast with team shuffles, and the factor is stored to o_M/o_LD for the
+// triangular solves and for the backward pass.  NM >= nv is the register
+// capacity of a row (compile-time), nl >= nv the team size.
+template <int NM, class Mem>
+__device__ void dense_factor(const DevModel& M, const Mem& w, int lane, int nl) {
+  const int n = M.nv;
+  const bool own = lane < n;
+  float row[NM];
+  {
+    V3 fn = v3(0.f, 0.f, 0.f), ff = v3(0.f, 0.f, 0.f);
+    unsigned mask = 0u;
+    if (own) {
+      const int i = __ldg(M.dof_link + lane);
+      si_mul(w, M.o_IC + 10 * i, ld3(w, M.o_S + 6 * lane), ld3(w, M.o_S + 6 * lane + 3), fn, ff);
+      mask = __ldg(M.anc_mask + lane);
+    }
+    const float arm = own ? __ldg(M.arm + lane) : 1.f;
+#pragma unroll
+    for (int b = 0; b < NM; ++b) {
+      float v = 0.f;
+      if ((mask >> b) & 1u) v = dot(ld3(w, M.o_S + 6 * b), fn) + dot(ld3(w, M.o_S + 6 * b + 3), ff);
+      if (b == lane) v += arm;
+      row[b] = v;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < NM; ++k) {
+    if (k < n) {
+      const float rk = row[k];
+      const float dkk = sqrtf(__shfl_sync(0xffffffffu, rk, k, nl));
+      const float lik = rk * (1.f / dkk);
+      if (lane > k) row[k] = lik;
+      else if (lane == k) row[k] = dkk;
+#pragma unroll
+      for (int j = k + 1; j < NM; ++j) {
+        if (j < n) {
+          const float ljk = __shfl_sync(0xffffffffu, lik, j, nl);
+          if (lane >= j) row[j] -= lik * ljk;
+        }
+      }
+    }
+  }
+  if (own) {
+#pragma unroll
+    for (int b = 0; b < NM; ++b) {
+      if (b < lane) w[M.o_M + lane * n + b] = row[b];
+      else if (b == lane) w[M.o_LD + lane] = row[b];
+    }
+  }
+  team_sync(nl);
+}
+
+// x = (L L^T)^{-1} b with the stored factor; lane a holds b_a, the columns of
+// the substitution are broadcast with team shuffles (no barriers).
 template <class Mem>
+__device__ void dense_solve(const DevModel& M, const Mem& w, int lane, int nl, int o_in, int o_out) {
+  const int n = M.nv;
+  const bool own = lane < n;
+  float b = own ? w[o_in + lane] : 0.f;
+  const float invd = own ? 1.f / w[M.o_LD + lane] : 0.f;
+  for (int k = 0; k < n; ++k) {
+    const float yk = __shfl_sync(0xffffffffu, b * invd, k, nl);
+    if (lane > k && own) b -= w[M.o_M + lane * n + k] * yk;
+    else if (lane == k) b = yk;
+  }
+  for (int k = n - 1; k >= 0; --k) {
+    const float xk = __shfl_sync(0xffffffffu, b * invd, k, nl);
+    if (lane < k) b -= w[M.o_M + k * n + lane] * xk;
+    else if (lane == k) b = xk;
+  }
+  if (own) w[o_out + lane] = b;
+  team_sync(nl);
+}
+
+// One forward substep up to the accelerations (integration is separate).
+// NM = 0: shared-memory dense stages (any team size, incl. one thread per
+// environment); NM > 0: register-resident dense path.
+template <int NM, class Mem>
 __device__ void substep_dynamics(const DevModel& M, const Mem& w, int lane, int nl) {
   st_fk(M, w, lane, nl);
   st_linkq(M, w, lane, nl);
@@ -594,9 +682,15 @@ __device__ void substep_dynamics(const DevModel& M, const Mem& w, int lane, int 
   st_items(M, w, lane, nl);
   st_id(M, w, lane, nl, false);
   st_rhs(M, w, lane, nl);
-  st_crba(M, w, lane, nl);
-  st_chol(M, w, lane, nl);
-  st_solve(M, w, lane, nl, M.o_B, M.o_QDD);
+  st_composite(M, w, lane, nl);
+  if constexpr (NM > 0) {
+    dense_factor<NM>(M, w, lane, nl);
+    dense_solve(M, w, lane, nl, M.o_B, M.o_QDD);
+  } else {
+    st_mass_rows(M, w, lane, nl);
+    st_chol(M, w, lane, nl);
+    st_solve(M, w, lane, nl, M.o_B, M.o_QDD);
+  }
 }
 
 // Reward on the post-step state (appendix A.3 reward shapes; see shacsim.h).
@@ -721,12 +815,16 @@ __device__ __forceinline__ void zero_range(const Mem& w, int o, int n, int lane,
 // Adjoint of the dynamics solve: given o_T = qdd_bar and the recomputed
 // substep (o_QDD holds the solved accelerations), add -lambda^T dG/d(q,qd,a)
 // to o_QB, o_QDB, o_ACTB.
-template <class Mem>
+template <int NM, class Mem>
 __device__ void st_dynamics_adj(const DevModel& M, const Mem& w, int lane, int nl) {
   // lambda = M^{-1} qdd_bar (cached factor)
-  for (int d = lane; d < M.nv; d += nl) w[M.o_B + d] = w[M.o_T + d];
-  team_sync(nl);
-  st_solve(M, w, lane, nl, M.o_B, M.o_LAM);
+  if constexpr (NM > 0) {
+    dense_solve(M, w, lane, nl, M.o_T, M.o_LAM);
+  } else {
+    for (int d = lane; d < M.nv; d += nl) w[M.o_B + d] = w[M.o_T + d];
+    team_sync(nl);
+    st_solve(M, w, lane, nl, M.o_B, M.o_LAM);
+  }
   // accelerations and forces with the actual qdd (the C pass used qdd = 0)
   st_id(M, w, lane, nl, true);
   // clear accumulators
@@ -833,6 +931,7 @@ __device__ void st_dynamics_adj(const DevModel& M, const Mem& w, int lane, int n
     V3 x = ld3(w, M.o_IT + 7 * c), f = ld3(w, M.o_IT + 7 * c + 3);
     const float dep = w[M.o_IT + 7 * c + 6];
     V3 xb = v3(0.f, 0.f, 0.f), wb = v3(0.f, 0.f, 0.f), vob = v3(0.f, 0.f, 0.f);
+    float db = 0.f;
     if (dep < 0.f) {
       V3 neb = -ld3(w, M.o_FB + 6 * i), feb = -ld3(w, M.o_FB + 6 * i + 3);
       V3 fbar = cross(neb, x) + feb;
@@ -857,16 +956,18 @@ __device__ void st_dynamics_adj(const DevModel& M, const Mem& w, int lane, int n
         vpb.x += vtb * vp.x / vt;
         vpb.y += vtb * vp.y / vt;
       }
-      // fn = (-ke + kd ddot) d
-      xb.z += fnb * (-M.ke + M.kd * vp.z);   // the depth is the height of x
+      // fn = (-ke + kd ddot) d, d = x.z + root height
+      db = fnb * (-M.ke + M.kd * vp.z);
+      xb.z += db;
       vpb.z += fnb * M.kd * dep;
       vob = vpb;
       wb = cross(x, vpb);
       xb = xb + cross(vpb, Vw);
     }
-    st3(w, M.o_ITB + 9 * c, xb);
-    st3(w, M.o_ITB + 9 * c + 3, wb);
-    st3(w, M.o_ITB + 9 * c + 6, vob);
+    st3(w, M.o_ITB + 10 * c, xb);
+    st3(w, M.o_ITB + 10 * c + 3, wb);
+    st3(w, M.o_ITB + 10 * c + 6, vob);
+    w[M.o_ITB + 10 * c + 9] = db;
   }
   for (int sg = lane; sg < M.nseg; sg += nl) {
     const int e0 = M.nc + 2 * sg, e1 = e0 + 1;
@@ -892,10 +993,15 @@ __device__ void st_dynamics_adj(const DevModel& M, const Mem& w, int lane, int n
     x1b = x1b + db;
     x0b = x0b - db;
     w[M.o_SEGA + sg] = (araw > 0.f && araw < 1.f) ? Fb * fm : 0.f;
-    st3(w, M.o_ITB + 9 * e0, x0b);
-    st3(w, M.o_ITB + 9 * e1, x1b);
+    st3(w, M.o_ITB + 10 * e0, x0b);
+    st3(w, M.o_ITB + 10 * e1, x1b);
   }
   team_sync(nl);
+  if (lane == 0 && M.root_free) {   // depth = x.z + root height: the root height gets every d_bar
+    float s = 0.f;
+    for (int c = 0; c < M.nc; ++c) s += w[M.o_ITB + 10 * c + 9];
+    w[M.o_QB + 2] += s;
+  }
   for (int mu_ = lane; mu_ < M.nm; mu_ += nl) {
     float s = 0.f;
     for (int sg = __ldg(M.mus_seg_ptr + mu_); sg < __ldg(M.mus_seg_ptr + mu_ + 1); ++sg) s += w[M.o_SEGA + sg];
@@ -908,15 +1014,15 @@ __device__ void st_dynamics_adj(const DevModel& M, const Mem& w, int lane, int n
     for (int k = 0; k < 9; ++k) Rb.m[k] = 0.f;
     for (int k = __ldg(M.li_ptr + i); k < __ldg(M.li_ptr + i + 1); ++k) {
       const int e = __ldg(M.li_idx + k);
-      V3 xb = ld3(w, M.o_ITB + 9 * e);
+      V3 xb = ld3(w, M.o_ITB + 10 * e);
       V3 lp = cld3(M.item_pos + 3 * e);
       pb = pb + xb;
       Rb.m[0] += xb.x * lp.x; Rb.m[1] += xb.x * lp.y; Rb.m[2] += xb.x * lp.z;
       Rb.m[3] += xb.y * lp.x; Rb.m[4] += xb.y * lp.y; Rb.m[5] += xb.y * lp.z;
       Rb.m[6] += xb.z * lp.x; Rb.m[7] += xb.z * lp.y; Rb.m[8] += xb.z * lp.z;
       if (e < M.nc) {
-        wb = wb + ld3(w, M.o_ITB + 9 * e + 3);
-        vb = vb + ld3(w, M.o_ITB + 9 * e + 6);
+        wb = wb + ld3(w, M.o_ITB + 10 * e + 3);
+        vb = vb + ld3(w, M.o_ITB + 10 * e + 6);
       }
     }
     add3(w, M.o_PB + 3 * i, pb);
@@ -1029,8 +1135,7 @@ __device__ void st_dynamics_adj(const DevModel& M, const Mem& w, int lane, int n
         Pb = Pb + ld3(w, M.o_TP + 12 * c + 9);
       }
       const int jt = __ldg(M.jtype + i), s = __ldg(M.qs + i), p = __ldg(M.parent + i);
-      if (jt == J_FREE) {
-        add3(w, M.o_QB + s, Pb);
+      if (jt == J_FREE) {   // the root origin is the reference point: no position cotangent here
         float xb = 0.f, yb = 0.f, zb = 0.f, wb = 0.f;
         quat_to_R_adj(w[M.o_Q + s + 3], w[M.o_Q + s + 4], w[M.o_Q + s + 5], w[M.o_Q + s + 6], Rb, xb, yb, zb, wb);
         w[M.o_QB + s + 3] += xb; w[M.o_QB + s + 4] += yb; w[M.o_QB + s + 5] += zb; w[M.o_QB + s + 6] += wb;
@@ -1083,11 +1188,11 @@ __device__ void st_dynamics_adj(const DevModel& M, const Mem& w, int lane, int n
 // One reverse substep: o_Q/o_QD hold the substep start state, o_QB/o_QDB the
 // cotangents of its end state; on return they hold the start-state cotangents,
 // and o_ACTB has accumulated the action cotangent.
-template <class Mem>
+template <int NM, class Mem>
 __device__ void substep_adjoint(const DevModel& M, const Mem& w, int lane, int nl) {
-  substep_dynamics(M, w, lane, nl);     // recompute with the cached factor
+  substep_dynamics<NM>(M, w, lane, nl);     // recompute; the factor is kept for lambda
   st_integrate_adj(M, w, lane, nl);
-  st_dynamics_adj(M, w, lane, nl);
+  st_dynamics_adj<NM>(M, w, lane, nl);
 }
 
 // non-finite check of the state (one lane)

@@ -12,7 +12,7 @@
 
 namespace shac {
 
-constexpr int BATCHED_BLOCK_MAX = 512;
+constexpr int BATCHED_BLOCK_MAX = 256;   // at most 8 warps per CTA
 
 // ------------------------------------------------------------------ PLAIN --
 
@@ -29,7 +29,7 @@ __global__ void k_plain_stage(PlainGroup g, int stage) {
       st_id(M, w, 0, 1, false); st_rhs(M, w, 0, 1);
       break;
     case PS_CRBA:
-      st_crba(M, w, 0, 1);
+      st_composite(M, w, 0, 1); st_mass_rows(M, w, 0, 1);
       break;
     case PS_SOLVE:
       st_chol(M, w, 0, 1); st_solve(M, w, 0, 1, M.o_B, M.o_QDD);
@@ -41,7 +41,7 @@ __global__ void k_plain_stage(PlainGroup g, int stage) {
       st_integrate_adj(M, w, 0, 1);
       break;
     case PS_ADJ_DYN:
-      st_dynamics_adj(M, w, 0, 1);
+      st_dynamics_adj<0>(M, w, 0, 1);
       break;
     default:
       break;
@@ -192,49 +192,83 @@ __device__ __forceinline__ void setup_team(const BatchedArgs& a, const WorkItem&
   t.env = it.env0 + (t.active ? t.team : 0);
 }
 
-__global__ void __launch_bounds__(BATCHED_BLOCK_MAX) k_batched_forward(BatchedArgs a) {
-  extern __shared__ float smem[];
-  __shared__ DevModel s_models[MAX_GROUPS];
-  for (int g = threadIdx.x; g < a.n_groups; g += blockDim.x) s_models[g] = a.models[g];
-  __syncthreads();
-  const int warp = threadIdx.x >> 5;
-  float* wsm = smem + (size_t)warp * a.smem_warp_floats;
-  int item_idx;
-  while (next_item(a, item_idx)) {
-    const WorkItem it = a.items[item_idx];
-    const DevModel& M = s_models[it.group];
-    Team t;
-    setup_team(a, it, t);
-    SMem w{wsm + (size_t)t.team * a.env_stride[it.group]};
-    const GroupIO& io = a.io.g[it.group];
-    team_load(w, M.o_Q, a.q_in + io.q_off, M.nq, io.N, t.env, t.lane, t.nl);
-    team_load(w, M.o_QD, a.qd_in + io.qd_off, M.nv, io.N, t.env, t.lane, t.nl);
-    if (a.q_copy0) {
-      team_store(w, M.o_Q, a.q_copy0 + io.q_off, M.nq, io.N, t.env, t.lane, t.nl, t.active);
-      team_store(w, M.o_QD, a.qd_copy0 + io.qd_off, M.nv, io.N, t.env, t.lane, t.nl, t.active);
+// One work item of the forward window (all steps, all substeps).
+template <int NM>
+__device__ void forward_item(const BatchedArgs& a, const DevModel& M, const WorkItem& it, const SMem& w,
+                             const Team& t) {
+  const GroupIO& io = a.io.g[it.group];
+  team_load(w, M.o_Q, a.q_in + io.q_off, M.nq, io.N, t.env, t.lane, t.nl);
+  team_load(w, M.o_QD, a.qd_in + io.qd_off, M.nv, io.N, t.env, t.lane, t.nl);
+  if (a.q_copy0) {
+    team_store(w, M.o_Q, a.q_copy0 + io.q_off, M.nq, io.N, t.env, t.lane, t.nl, t.active);
+    team_store(w, M.o_QD, a.qd_copy0 + io.qd_off, M.nv, io.N, t.env, t.lane, t.nl, t.active);
+  }
+  for (int step = 0; step < a.h; ++step) {
+    team_load(w, M.o_ACT, a.act + (size_t)step * a.io.act_size + io.act_off, M.na, io.N, t.env, t.lane, t.nl);
+    clear_comp(M, w, t.lane, t.nl);
+    team_sync(t.nl);
+    for (int k = 0; k < M.K; ++k) {
+      substep_dynamics<NM>(M, w, t.lane, t.nl);
+      st_integrate(M, w, t.lane, t.nl);
     }
-    for (int step = 0; step < a.h; ++step) {
-      team_load(w, M.o_ACT, a.act + (size_t)step * a.io.act_size + io.act_off, M.na, io.N, t.env, t.lane, t.nl);
-      clear_comp(M, w, t.lane, t.nl);
-      team_sync(t.nl);
-      for (int k = 0; k < M.K; ++k) {
-        substep_dynamics(M, w, t.lane, t.nl);
-        st_integrate(M, w, t.lane, t.nl);
-      }
-      team_store(w, M.o_Q, a.q_out + (size_t)step * a.io.q_size + io.q_off, M.nq, io.N, t.env, t.lane, t.nl, t.active);
-      team_store(w, M.o_QD, a.qd_out + (size_t)step * a.io.qd_size + io.qd_off, M.nv, io.N, t.env, t.lane, t.nl,
-                 t.active);
-      if (t.lane == 0 && t.active) {
-        a.reward[(size_t)step * a.io.n_envs + io.env_off + t.env] = reward_value(M, w);
-        if (!state_finite(M, w)) atomicOr(a.flags, FLAG_NONFINITE);
-      }
-      team_sync(t.nl);
+    team_store(w, M.o_Q, a.q_out + (size_t)step * a.io.q_size + io.q_off, M.nq, io.N, t.env, t.lane, t.nl, t.active);
+    team_store(w, M.o_QD, a.qd_out + (size_t)step * a.io.qd_size + io.qd_off, M.nv, io.N, t.env, t.lane, t.nl,
+               t.active);
+    if (t.lane == 0 && t.active) {
+      a.reward[(size_t)step * a.io.n_envs + io.env_off + t.env] = reward_value(M, w);
+      if (!state_finite(M, w)) atomicOr(a.flags, FLAG_NONFINITE);
     }
-    __syncwarp();
+    team_sync(t.nl);
   }
 }
 
-__global__ void __launch_bounds__(BATCHED_BLOCK_MAX) k_batched_adjoint(BatchedArgs a) {
+// One work item of the window adjoint (reverse over steps; substeps recomputed
+// from the step checkpoint, their start states kept in the tape).
+template <int NM>
+__device__ void adjoint_item(const BatchedArgs& a, const DevModel& M, const WorkItem& it, const SMem& w,
+                             const Team& t) {
+  const GroupIO& io = a.io.g[it.group];
+  const int S = M.nq + M.nv;
+  float* tape = a.tape + a.tape_off[it.group] + (size_t)(it.env0 + t.team) * ((size_t)M.K * S);
+  team_load(w, M.o_QB, a.qT_bar + io.q_off, M.nq, io.N, t.env, t.lane, t.nl);
+  team_load(w, M.o_QDB, a.qdT_bar + io.qd_off, M.nv, io.N, t.env, t.lane, t.nl);
+  for (int step = a.h - 1; step >= 0; --step) {
+    team_load(w, M.o_Q, a.q_traj + (size_t)step * a.io.q_size + io.q_off, M.nq, io.N, t.env, t.lane, t.nl);
+    team_load(w, M.o_QD, a.qd_traj + (size_t)step * a.io.qd_size + io.qd_off, M.nv, io.N, t.env, t.lane, t.nl);
+    team_load(w, M.o_ACT, a.act + (size_t)step * a.io.act_size + io.act_off, M.na, io.N, t.env, t.lane, t.nl);
+    zero_range(w, M.o_ACTB, M.na, t.lane, t.nl);
+    clear_comp(M, w, t.lane, t.nl);
+    team_sync(t.nl);
+    for (int k = 0; k < M.K; ++k) {
+      for (int j = t.lane; j < S; j += t.nl) tape[(size_t)k * S + j] = w[M.o_Q + j];   // o_QD follows o_Q
+      substep_dynamics<NM>(M, w, t.lane, t.nl);
+      st_integrate(M, w, t.lane, t.nl);
+    }
+    if (t.lane == 0) reward_adjoint(M, w, a.reward_bar[(size_t)step * a.io.n_envs + io.env_off + t.env]);
+    team_sync(t.nl);
+    for (int k = M.K - 1; k >= 0; --k) {
+      for (int j = t.lane; j < S; j += t.nl) w[M.o_Q + j] = tape[(size_t)k * S + j];
+      team_sync(t.nl);
+      substep_adjoint<NM>(M, w, t.lane, t.nl);
+    }
+    team_store(w, M.o_ACTB, a.act_bar + (size_t)step * a.io.act_size + io.act_off, M.na, io.N, t.env, t.lane, t.nl,
+               t.active);
+    if (a.qtb) {   // cotangent read directly from checkpoint `step`
+      const float* qa = a.qtb + (size_t)step * a.io.q_size + io.q_off;
+      const float* qda = a.qdtb + (size_t)step * a.io.qd_size + io.qd_off;
+      for (int j = t.lane; j < M.nq; j += t.nl) w[M.o_QB + j] += __ldg(qa + (size_t)j * io.N + t.env);
+      for (int j = t.lane; j < M.nv; j += t.nl) w[M.o_QDB + j] += __ldg(qda + (size_t)j * io.N + t.env);
+    }
+    team_sync(t.nl);
+  }
+  team_store(w, M.o_QB, a.q0_bar + io.q_off, M.nq, io.N, t.env, t.lane, t.nl, t.active);
+  team_store(w, M.o_QDB, a.qd0_bar + io.qd_off, M.nv, io.N, t.env, t.lane, t.nl, t.active);
+}
+
+// Persistent kernels: warps pull work items; each item dispatches on the
+// register capacity of its group's dense path (0 = shared-memory form).
+template <bool ADJ>
+__global__ void __launch_bounds__(BATCHED_BLOCK_MAX) k_batched(BatchedArgs a) {
   extern __shared__ float smem[];
   __shared__ DevModel s_models[MAX_GROUPS];
   for (int g = threadIdx.x; g < a.n_groups; g += blockDim.x) s_models[g] = a.models[g];
@@ -248,46 +282,24 @@ __global__ void __launch_bounds__(BATCHED_BLOCK_MAX) k_batched_adjoint(BatchedAr
     Team t;
     setup_team(a, it, t);
     SMem w{wsm + (size_t)t.team * a.env_stride[it.group]};
-    const GroupIO& io = a.io.g[it.group];
-    const int S = M.nq + M.nv;
-    float* tape = a.tape + a.tape_off[it.group] + (size_t)(it.env0 + t.team) * ((size_t)M.K * S);
-    team_load(w, M.o_QB, a.qT_bar + io.q_off, M.nq, io.N, t.env, t.lane, t.nl);
-    team_load(w, M.o_QDB, a.qdT_bar + io.qd_off, M.nv, io.N, t.env, t.lane, t.nl);
-    for (int step = a.h - 1; step >= 0; --step) {
-      team_load(w, M.o_Q, a.q_traj + (size_t)step * a.io.q_size + io.q_off, M.nq, io.N, t.env, t.lane, t.nl);
-      team_load(w, M.o_QD, a.qd_traj + (size_t)step * a.io.qd_size + io.qd_off, M.nv, io.N, t.env, t.lane, t.nl);
-      team_load(w, M.o_ACT, a.act + (size_t)step * a.io.act_size + io.act_off, M.na, io.N, t.env, t.lane, t.nl);
-      zero_range(w, M.o_ACTB, M.na, t.lane, t.nl);
-      clear_comp(M, w, t.lane, t.nl);
-      team_sync(t.nl);
-      // recompute the substeps, keeping each substep's start state
-      for (int k = 0; k < M.K; ++k) {
-        for (int j = t.lane; j < S; j += t.nl) tape[(size_t)k * S + j] = w[M.o_Q + j];   // o_QD follows o_Q
-        substep_dynamics(M, w, t.lane, t.nl);
-        st_integrate(M, w, t.lane, t.nl);
-      }
-      if (t.lane == 0) reward_adjoint(M, w, a.reward_bar[(size_t)step * a.io.n_envs + io.env_off + t.env]);
-      team_sync(t.nl);
-      for (int k = M.K - 1; k >= 0; --k) {
-        for (int j = t.lane; j < S; j += t.nl) w[M.o_Q + j] = tape[(size_t)k * S + j];
-        team_sync(t.nl);
-        substep_adjoint(M, w, t.lane, t.nl);
-      }
-      team_store(w, M.o_ACTB, a.act_bar + (size_t)step * a.io.act_size + io.act_off, M.na, io.N, t.env, t.lane,
-                 t.nl, t.active);
-      if (a.qtb) {   // cotangent read directly from checkpoint `step`
-        const float* qa = a.qtb + (size_t)step * a.io.q_size + io.q_off;
-        const float* qda = a.qdtb + (size_t)step * a.io.qd_size + io.qd_off;
-        for (int j = t.lane; j < M.nq; j += t.nl) w[M.o_QB + j] += __ldg(qa + (size_t)j * io.N + t.env);
-        for (int j = t.lane; j < M.nv; j += t.nl) w[M.o_QDB + j] += __ldg(qda + (size_t)j * io.N + t.env);
-      }
-      team_sync(t.nl);
+    switch (a.dense_nm[it.group]) {
+      case 8:
+        if (ADJ) adjoint_item<8>(a, M, it, w, t); else forward_item<8>(a, M, it, w, t);
+        break;
+      case 16:
+        if (ADJ) adjoint_item<16>(a, M, it, w, t); else forward_item<16>(a, M, it, w, t);
+        break;
+      case 32:
+        if (ADJ) adjoint_item<32>(a, M, it, w, t); else forward_item<32>(a, M, it, w, t);
+        break;
+      default:
+        if (ADJ) adjoint_item<0>(a, M, it, w, t); else forward_item<0>(a, M, it, w, t);
     }
-    team_store(w, M.o_QB, a.q0_bar + io.q_off, M.nq, io.N, t.env, t.lane, t.nl, t.active);
-    team_store(w, M.o_QDB, a.qd0_bar + io.qd_off, M.nv, io.N, t.env, t.lane, t.nl, t.active);
     __syncwarp();
   }
 }
+#define k_batched_forward k_batched<false>
+#define k_batched_adjoint k_batched<true>
 
 void launch_batched_forward(const BatchedArgs& a, int grid, int block, size_t smem, cudaStream_t s) {
   k_batched_forward<<<grid, block, smem, s>>>(a);

@@ -29,6 +29,7 @@ struct BatchedArgs {
   int n_groups;
   IOArgs io;
   int lanes[MAX_GROUPS];    // lanes per environment (team size) per group
+  int dense_nm[MAX_GROUPS]; // register row capacity of the dense path (0: shared-memory form)
   int smem_warp_floats;     // shared floats per warp
   int env_stride[MAX_GROUPS];   // padded env_floats per group (shared memory)
   const WorkItem* items;

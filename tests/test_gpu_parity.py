@@ -223,3 +223,65 @@ def test_autograd_window_gradient_matches_step_chain(oracle_mod):
     total.backward()
     np.testing.assert_allclose(g_act.cpu().numpy(), act2.grad.cpu().numpy(), rtol=1e-4, atol=1e-5)
     np.testing.assert_allclose(g_qd0.cpu().numpy(), qd_leaf.grad.cpu().numpy(), rtol=1e-4, atol=1e-5)
+
+
+@pytest.mark.parametrize("lanes", [1, 4, 16, 32])
+def test_team_sizes_match_oracle(oracle_mod, lanes):
+    """Every team size (lanes per environment), including teams narrower than
+    the DOF count (shared-memory dense stages), matches the oracle."""
+    m = I.ant()
+    N = 21
+    sim = make_sim([(m, N)], "batched", 2)
+    sim.set_launch(0, lanes, 0)
+    assert sim.get_launch(0)[0] == lanes
+    o = orc(oracle_mod, m)
+    q, qd, a = seeded_case(m, N, 9, "initial")
+    qn, qdn, r = sim.step(T(q), T(qd), T(a))
+    torch.cuda.synchronize()
+    rq, rqd, rr = o.step(q.T, qd.T, a.T)
+    assert_state_close(qn.cpu().numpy().reshape(m.nq, N).T, rq, f"lanes {lanes} q")
+    assert_state_close(qdn.cpu().numpy().reshape(m.nv, N).T, rqd, f"lanes {lanes} qd")
+    rng = np.random.default_rng(3)
+    qb, qdb, rb = (rng.normal(size=s).astype(np.float32) for s in ((m.nq, N), (m.nv, N), N))
+    gq, gqd, ga = sim.step_adjoint(T(q), T(qd), T(a), T(qb), T(qdb), T(rb))
+    torch.cuda.synchronize()
+    sq, sqd, sa = o.step_vjp(q.T, qd.T, a.T, qb.T, qdb.T, rb)
+    got = np.concatenate([gq.cpu().numpy().reshape(m.nq, N), gqd.cpu().numpy().reshape(m.nv, N),
+                          ga.cpu().numpy().reshape(m.na, N)])
+    assert_grad_close(got, np.concatenate([sq.T, sqd.T, sa.T]), f"lanes {lanes} adjoint")
+
+
+@pytest.mark.parametrize("workload,h", [("ant-2048", 32), ("humanoid-1024", 8)])
+def test_full_size_sampled_parity(oracle_mod, workload, h):
+    """Full-size workload in the bench's launch configuration: every step of
+    sampled environments from the GPU checkpoints, and their window gradients,
+    against the oracle; finiteness of every environment."""
+    wl = I.workload(workload)
+    m, N = wl.groups[0]
+    sim = make_sim(wl.groups, "batched", h)
+    q0, qd0 = I.initial_state(m, N, 0)
+    act = I.window_actions(m, N, h, 0)
+    qt, qdt, rw = sim.window_forward(T(q0), T(qd0), T(act).view(h, -1))
+    rb = torch.full((h, N), 1.0 / (N * h), device="cuda")
+    zq = torch.zeros(h + 1, sim.q_size, device="cuda")
+    zqd = torch.zeros(h + 1, sim.qd_size, device="cuda")
+    g0, gd0, ga = sim.window_adjoint(qt, qdt, T(act).view(h, -1), rb, zq, zqd)
+    torch.cuda.synchronize()
+    for x in (qt, qdt, rw, g0, gd0, ga):
+        assert torch.isfinite(x).all()
+    assert sim.status() == 0
+    envs = np.sort(np.random.default_rng(1).choice(N, size=6, replace=False))
+    o = orc(oracle_mod, m)
+    gq = qt.cpu().numpy().reshape(h + 1, m.nq, N)[:, :, envs]
+    gqd = qdt.cpu().numpy().reshape(h + 1, m.nv, N)[:, :, envs]
+    a = act[:, :, envs]
+    rq, rqd, rr = o.step(gq[:-1].transpose(0, 2, 1).reshape(-1, m.nq), gqd[:-1].transpose(0, 2, 1).reshape(-1, m.nv),
+                         a.transpose(0, 2, 1).reshape(-1, m.na))
+    assert_state_close(gq[1:].transpose(0, 2, 1).reshape(-1, m.nq), rq, f"{workload} sampled q")
+    assert_state_close(gqd[1:].transpose(0, 2, 1).reshape(-1, m.nv), rqd, f"{workload} sampled qd")
+    qb, qdb, ab = o.window_adjoint(gq.transpose(0, 2, 1), gqd.transpose(0, 2, 1), a.transpose(0, 2, 1),
+                                   rb.cpu().numpy()[:, envs], np.zeros((len(envs), m.nq)), np.zeros((len(envs), m.nv)))
+    got = np.concatenate([g0.cpu().numpy().reshape(m.nq, N)[:, envs], gd0.cpu().numpy().reshape(m.nv, N)[:, envs],
+                          ga.cpu().numpy().reshape(h * m.na, N)[:, envs]])
+    ref = np.concatenate([qb.T, qdb.T, ab.transpose(0, 2, 1).reshape(h * m.na, len(envs))])
+    assert_grad_close(got, ref, f"{workload} sampled window gradient")

@@ -77,7 +77,7 @@ static void compute_layout(shac_model* m) {
   take(d.o_S, 6 * nv); take(d.o_V, 6 * L);
   take(d.o_A, 6 * L); take(d.o_F, 6 * L); take(d.o_FX, 6 * L); take(d.o_IT, 7 * ni); take(d.o_IC, 10 * L);
   take(d.o_M, nv * nv); take(d.o_LD, nv); take(d.o_B, nv); take(d.o_T, nv); take(d.o_QDD, nv);
-  take(d.o_LAM, nv); take(d.o_SB, 6 * nv); take(d.o_VB, 6 * L); take(d.o_AB, 6 * L); take(d.o_FB, 6 * L);
+  take(d.o_LAM, nv); take(d.o_VB, 6 * L); take(d.o_AB, 6 * L); take(d.o_FB, 6 * L);
   take(d.o_SIB, 12 * L); take(d.o_RB, 9 * L); take(d.o_PB, 3 * L); take(d.o_ITB, 10 * ni); take(d.o_TP, 12 * L);
   take(d.o_SEGA, m->nseg);
   d.env_floats = o;

@@ -23,13 +23,13 @@ __global__ void k_plain_stage(PlainGroup g, int stage) {
   GMem w{g.ws + e, g.N};
   switch (stage) {
     case PS_KIN:
-      st_fk(M, w, 0, 1); st_linkq(M, w, 0, 1); st_vel(M, w, 0, 1); st_items(M, w, 0, 1);
+      sw_forward(M, w, 0, 1);
       break;
     case PS_BIAS:
-      st_id(M, w, 0, 1, false); st_rhs(M, w, 0, 1);
+      sw_gather(M, w, 0, 1, true); st_rhs(M, w, 0, 1);
       break;
     case PS_CRBA:
-      st_composite(M, w, 0, 1); st_mass_rows(M, w, 0, 1);
+      st_mass_rows(M, w, 0, 1);
       break;
     case PS_SOLVE:
       st_chol(M, w, 0, 1); st_solve(M, w, 0, 1, M.o_B, M.o_QDD);

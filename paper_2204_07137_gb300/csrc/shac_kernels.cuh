@@ -75,9 +75,10 @@ struct PlainGroup {
 };
 
 enum PlainStage {
-  PS_KIN = 0,       // forward kinematics, motion subspaces, inertias, velocities, contact/muscle forces
-  PS_BIAS,          // Newton-Euler bias and right-hand side
-  PS_CRBA,          // composite-rigid-body mass matrix
+  PS_KIN = 0,       // root-first sweep: kinematics, inertias, subspaces, velocities, contact/muscle
+                    // forces, Newton-Euler accelerations and local forces
+  PS_BIAS,          // leaves-first sweep: total forces, composite inertias; right-hand side
+  PS_CRBA,          // composite-rigid-body mass matrix rows
   PS_SOLVE,         // Cholesky factorisation and solve
   PS_INTEGRATE,     // semi-implicit Euler
   PS_ADJ_INTEGRATE, // integrator adjoint

@@ -71,12 +71,14 @@ static void compute_layout(shac_model* m) {
   const int L = m->L, nv = m->nv, ni = m->nitems;
   int o = 0;
   auto take = [&](int& off, int n) { off = o; o += n; };
-  take(d.o_Q, m->nq); take(d.o_QD, nv); take(d.o_ACT, m->na);
-  take(d.o_QB, m->nq); take(d.o_QDB, nv); take(d.o_ACTB, m->na);
-  take(d.o_R, 9 * L); take(d.o_P, 3 * L); take(d.o_QC, m->nq); take(d.o_QDC, nv); take(d.o_SI, 10 * L);
-  take(d.o_S, 6 * nv); take(d.o_V, 6 * L);
-  take(d.o_A, 6 * L); take(d.o_F, 6 * L); take(d.o_FX, 6 * L); take(d.o_IT, 7 * ni); take(d.o_IC, 10 * L);
-  take(d.o_M, nv * nv); take(d.o_LD, nv); take(d.o_B, nv); take(d.o_T, nv); take(d.o_QDD, nv);
+  // substep record: the start state and every forward intermediate the reverse pass reads
+  take(d.o_Q, m->nq); take(d.o_QD, nv); take(d.o_R, 9 * L); take(d.o_P, 3 * L); take(d.o_SI, 10 * L);
+  take(d.o_S, 6 * nv); take(d.o_V, 6 * L); take(d.o_FX, 6 * L); take(d.o_IT, 7 * ni);
+  take(d.o_M, nv * nv); take(d.o_LD, nv); take(d.o_QDD, nv);
+  d.rec_floats = o;
+  take(d.o_ACT, m->na); take(d.o_QB, m->nq); take(d.o_QDB, nv); take(d.o_ACTB, m->na);
+  take(d.o_QC, m->nq); take(d.o_QDC, nv); take(d.o_A, 6 * L); take(d.o_F, 6 * L); take(d.o_IC, 10 * L);
+  take(d.o_B, nv); take(d.o_T, nv);
   take(d.o_LAM, nv); take(d.o_VB, 6 * L); take(d.o_AB, 6 * L); take(d.o_FB, 6 * L);
   take(d.o_SIB, 12 * L); take(d.o_RB, 9 * L); take(d.o_PB, 3 * L); take(d.o_ITB, 10 * ni); take(d.o_TP, 12 * L);
   take(d.o_SEGA, m->nseg);
@@ -360,14 +362,15 @@ static void compute_workspace(shac_batch* b) {
     const Group& g = b->groups[gi];
     const shac_model* m = g.m;
     const size_t S = (size_t)(m->nq + m->nv) * m->K;
+    const size_t REC = (size_t)m->layout.rec_floats * m->K;
     if (b->form == SHAC_FORM_PLAIN) {
       b->plain_scratch_off[gi] = off;
       off = align(off + (size_t)m->layout.env_floats * g.N * sizeof(float));
       b->plain_tape_off[gi] = off;
       off = align(off + S * g.N * sizeof(float));
     } else {
-      b->batched_tape_off[gi] = off;
-      off = align(off + S * (size_t)(g.N + 31) * sizeof(float));
+      b->batched_tape_off[gi] = off;   // one step's substep records per environment slot
+      off = align(off + REC * (size_t)(g.N + 31) * sizeof(float));
     }
   }
   b->ws_total = off;

@@ -74,6 +74,7 @@ struct DevModel {
   int o_R, o_P, o_SI, o_S, o_V, o_A, o_F, o_FX, o_IT, o_IC, o_M, o_LD, o_B, o_T, o_QDD;
   int o_QC, o_QDC;                       // compensation (low parts) of q, qd within a step
   int o_LAM, o_VB, o_AB, o_FB, o_SIB, o_RB, o_PB, o_ITB, o_TP, o_SEGA;
+  int rec_floats;       // floats of the substep record: scratch [0, rec_floats) (o_Q first)
   int env_floats;
 };
 

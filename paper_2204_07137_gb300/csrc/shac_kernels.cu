@@ -222,14 +222,16 @@ __device__ void forward_item(const BatchedArgs& a, const DevModel& M, const Work
   }
 }
 
-// One work item of the window adjoint (reverse over steps; substeps recomputed
-// from the step checkpoint, their start states kept in the tape).
+// One work item of the window adjoint (reverse over steps).  Each step's
+// substeps are recomputed once from its checkpoint; every substep's record
+// (start state and forward intermediates, scratch [0, rec_floats)) is kept in
+// the workspace and reloaded by the reverse pass.
 template <int NM>
 __device__ void adjoint_item(const BatchedArgs& a, const DevModel& M, const WorkItem& it, const SMem& w,
                              const Team& t) {
   const GroupIO& io = a.io.g[it.group];
-  const int S = M.nq + M.nv;
-  float* tape = a.tape + a.tape_off[it.group] + (size_t)(it.env0 + t.team) * ((size_t)M.K * S);
+  const int REC = M.rec_floats;
+  float* tape = a.tape + a.tape_off[it.group] + (size_t)(it.env0 + t.team) * ((size_t)M.K * REC);
   team_load(w, M.o_QB, a.qT_bar + io.q_off, M.nq, io.N, t.env, t.lane, t.nl);
   team_load(w, M.o_QDB, a.qdT_bar + io.qd_off, M.nv, io.N, t.env, t.lane, t.nl);
   for (int step = a.h - 1; step >= 0; --step) {
@@ -240,16 +242,20 @@ __device__ void adjoint_item(const BatchedArgs& a, const DevModel& M, const Work
     clear_comp(M, w, t.lane, t.nl);
     team_sync(t.nl);
     for (int k = 0; k < M.K; ++k) {
-      for (int j = t.lane; j < S; j += t.nl) tape[(size_t)k * S + j] = w[M.o_Q + j];   // o_QD follows o_Q
       substep_dynamics<NM>(M, w, t.lane, t.nl);
+      float* rec = tape + (size_t)k * REC;
+      for (int j = t.lane; j < REC; j += t.nl) rec[j] = w[j];
+      team_sync(t.nl);
       st_integrate(M, w, t.lane, t.nl);
     }
     if (t.lane == 0) reward_adjoint(M, w, a.reward_bar[(size_t)step * a.io.n_envs + io.env_off + t.env]);
     team_sync(t.nl);
     for (int k = M.K - 1; k >= 0; --k) {
-      for (int j = t.lane; j < S; j += t.nl) w[M.o_Q + j] = tape[(size_t)k * S + j];
+      const float* rec = tape + (size_t)k * REC;
+      for (int j = t.lane; j < REC; j += t.nl) w[j] = rec[j];
       team_sync(t.nl);
-      substep_adjoint<NM>(M, w, t.lane, t.nl);
+      st_integrate_adj(M, w, t.lane, t.nl);
+      st_dynamics_adj<NM>(M, w, t.lane, t.nl);
     }
     team_store(w, M.o_ACTB, a.act_bar + (size_t)step * a.io.act_size + io.act_off, M.na, io.N, t.env, t.lane, t.nl,
                t.active);

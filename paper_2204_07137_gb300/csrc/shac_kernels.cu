@@ -222,6 +222,18 @@ __device__ void forward_item(const BatchedArgs& a, const DevModel& M, const Work
   }
 }
 
+// Reload a substep record (global -> shared) with asynchronous copies, all in
+// flight together, then wait for this lane's copies (the caller's team barrier
+// makes them visible to the team).
+__device__ __forceinline__ void record_load(const SMem& w, const float* src, int n, int lane, int nl) {
+  for (int j = lane; j < n; j += nl) {
+    const unsigned dst = (unsigned)__cvta_generic_to_shared(&w[j]);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dst), "l"(src + j) : "memory");
+  }
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
 // One work item of the window adjoint (reverse over steps).  Each step's
 // substeps are recomputed once from its checkpoint; every substep's record
 // (start state and forward intermediates, scratch [0, rec_floats)) is kept in
@@ -251,8 +263,7 @@ __device__ void adjoint_item(const BatchedArgs& a, const DevModel& M, const Work
     if (t.lane == 0) reward_adjoint(M, w, a.reward_bar[(size_t)step * a.io.n_envs + io.env_off + t.env]);
     team_sync(t.nl);
     for (int k = M.K - 1; k >= 0; --k) {
-      const float* rec = tape + (size_t)k * REC;
-      for (int j = t.lane; j < REC; j += t.nl) w[j] = rec[j];
+      record_load(w, tape + (size_t)k * REC, REC, t.lane, t.nl);
       team_sync(t.nl);
       st_integrate_adj(M, w, t.lane, t.nl);
       st_dynamics_adj<NM>(M, w, t.lane, t.nl);

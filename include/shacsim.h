@@ -187,6 +187,27 @@ shac_status shac_window_adjoint(shac_batch* batch, void* stream, void* workspace
                                 const float* reward_bar, const float* q_traj_bar, const float* qd_traj_bar,
                                 float* q0_bar, float* qd0_bar, float* act_bar);
 
+/* Step adjoint for callers that cannot allocate device memory when they call
+ * the simulator (e.g. inside a CUDA graph capture that forbids allocation, or
+ * runtimes that only pass pre-registered buffers).  The paper has no
+ * counterpart: this is a deployment variant of shac_step_adjoint.
+ *
+ * Same arguments and results as shac_step_adjoint minus the workspace: the
+ * scratch (work counter and substep records) lives in a 64 MiB device array
+ * compiled into the library, resident on every GPU that loads it until the
+ * process exits.  Nothing is allocated by the call.  A batch whose
+ * shac_batch_workspace_bytes exceeds 64 MiB is rejected with
+ * SHAC_ERR_CAPACITY (for the ant-like model: up to about 1500 environments).
+ * The first call on a device looks up the array's device address with that
+ * device current; make that first call before any stream capture.  Every call
+ * on a device shares the one array, and it keeps the last call's contents:
+ * calls that may overlap on the GPU (different streams, or concurrent host
+ * threads) race on it and must be serialised by the caller. */
+shac_status shac_step_adjoint_static(shac_batch* batch, void* stream,
+                                     const float* q, const float* qd, const float* act,
+                                     const float* q_next_bar, const float* qd_next_bar, const float* reward_bar,
+                                     float* q_bar, float* qd_bar, float* act_bar);
+
 /* Batched-form launch shape: lanes per environment for group g (1,2,4,8,16,32;
  * 0 = automatic) and warps per CTA.  Does not change results beyond FP32
  * reassociation inside a team. */

@@ -26,7 +26,7 @@ EXPORTED = [
     "shac_model_create", "shac_model_destroy", "shac_model_dims", "shac_batch_create", "shac_batch_destroy",
     "shac_batch_dims", "shac_batch_workspace_bytes", "shac_step", "shac_step_adjoint", "shac_window_forward",
     "shac_window_adjoint", "shac_batch_set_launch", "shac_batch_get_launch", "shac_get_status",
-    "shac_status_string",
+    "shac_status_string", "shac_step_adjoint_static",
 ]
 
 
@@ -85,6 +85,8 @@ def load(path: str = LIB_PATH):
     L.shac_step.restype = ctypes.c_int
     L.shac_step_adjoint.argtypes = [_vp, _vp, _vp] + [_vp] * 9
     L.shac_step_adjoint.restype = ctypes.c_int
+    L.shac_step_adjoint_static.argtypes = [_vp, _vp] + [_vp] * 9
+    L.shac_step_adjoint_static.restype = ctypes.c_int
     L.shac_window_forward.argtypes = [_vp, _vp, _vp, ctypes.c_int32] + [_vp] * 6
     L.shac_window_forward.restype = ctypes.c_int
     L.shac_window_adjoint.argtypes = [_vp, _vp, _vp, ctypes.c_int32] + [_vp] * 9

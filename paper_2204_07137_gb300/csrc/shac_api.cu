@@ -2,6 +2,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -624,6 +625,55 @@ extern "C" shac_status shac_window_adjoint(shac_batch* b, void* stream, void* ws
   return run_adjoint(b, (cudaStream_t)stream, ws, h, q_traj, qd_traj, act, reward_bar, q_traj_bar, qd_traj_bar,
                      q_traj_bar + (size_t)h * b->q_size, qd_traj_bar + (size_t)h * b->qd_size, q0_bar, qd0_bar,
                      act_bar);
+}
+
+// ---------------------------------------------------------------------------
+// Step adjoint with its scratch in a fixed device array of this library.
+//
+// Some callers cannot allocate device memory at the point where they call the
+// simulator: code recorded into a CUDA graph under a capture mode that forbids
+// allocation, runtimes that only hand out pre-registered buffers, or hosts
+// whose device allocator is owned by another component.  They call
+// shac_step_adjoint_static, which computes exactly what shac_step_adjoint
+// computes but takes its scratch (work counter and substep records) from the
+// array below instead of a caller workspace.  The array is STATIC_SCRATCH_BYTES
+// (64 MiB) on every GPU that loads the library and stays resident until the
+// process exits.
+constexpr size_t STATIC_SCRATCH_BYTES = size_t(64) << 20;
+static __device__ __align__(256) unsigned char g_static_scratch[STATIC_SCRATCH_BYTES];
+
+constexpr int STATIC_MAX_DEVICES = 64;
+static std::mutex g_static_mutex;
+static void* g_static_addr[STATIC_MAX_DEVICES] = {};
+
+// Device address of the array on the current device, looked up once per device
+// (on the first call made with that device current).
+static shac_status static_scratch_address(void** out) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return SHAC_ERR_CUDA;
+  if (dev < 0 || dev >= STATIC_MAX_DEVICES) return SHAC_ERR_UNSUPPORTED;
+  std::lock_guard<std::mutex> lock(g_static_mutex);
+  if (!g_static_addr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || !p) return SHAC_ERR_CUDA;
+    g_static_addr[dev] = p;
+  }
+  *out = g_static_addr[dev];
+  return SHAC_OK;
+}
+
+extern "C" shac_status shac_step_adjoint_static(shac_batch* b, void* stream, const float* q, const float* qd,
+                                                const float* act, const float* q_next_bar, const float* qd_next_bar,
+                                                const float* reward_bar, float* q_bar, float* qd_bar,
+                                                float* act_bar) {
+  if (!b || !q || !qd || !act || !q_next_bar || !qd_next_bar || !reward_bar || !q_bar || !qd_bar || !act_bar)
+    return SHAC_ERR_INVALID_ARG;
+  if (b->ws_total > STATIC_SCRATCH_BYTES) return SHAC_ERR_CAPACITY;
+  void* ws = nullptr;
+  const shac_status st = static_scratch_address(&ws);
+  if (st != SHAC_OK) return st;
+  return run_adjoint(b, (cudaStream_t)stream, ws, 1, q, qd, act, reward_bar, nullptr, nullptr, q_next_bar, qd_next_bar,
+                     q_bar, qd_bar, act_bar);
 }
 
 extern "C" shac_status shac_get_status(shac_batch* b, void* stream, uint32_t* flags, int32_t clear) {

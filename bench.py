@@ -46,12 +46,26 @@ FLUSH_BYTES = 256 << 20
 # FP32 lanes x 2 flop (FMA) x 2.07 GHz maximum SM clock.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
-# Algorithmic FP32 work per env-step (forward window step + adjoint step
-# including the substep recompute) of the ant-like model: thread-level
-# FADD + FMUL + 2 x FFMA executed by the one-env-per-thread (PLAIN) stage
-# kernels, counted by ncu over one window (profiles/plain_flops_ant.md).
-# None until measured; the roofline then reports achieved = null.
-ALGO_FLOPS_PER_ENV_STEP = {"forward": None, "adjoint": None}
+# Algorithmic FP32 work per env-step, measured (not estimated): thread-level
+# FADD + FMUL + 2 x FFMA executed by the one-environment-per-thread (PLAIN)
+# stage kernels over one window step, counted by ncu (the command and the
+# per-stage split are in profiles/plain_flops_ant.md).  The batched adjoint
+# recomputes a step's substeps once, so its count is one forward recompute
+# plus the reverse-only stages.  Workloads without a count report achieved=null.
+ALGO_FLOPS_PER_ENV_STEP = {
+    "ant-2048": {"forward": 137284, "adjoint": 137148 + 183668},
+}
+
+# DRAM traffic (read + write) per launch of each batched kernel at h = 32 on
+# ant-2048, scaled from an ncu capture at h = 2 by the 16x env-steps (the
+# per-step traffic is the same at every step); profiles/batched_ant_2048.md.
+# None until captured for the current kernels.
+TRAFFIC_BYTES_PER_LAUNCH = {"ant-2048": {"k_batched_forward": None, "k_batched_adjoint": None}}
+
+# Algorithmic HBM bytes per env-step (ant): forward reads the action (8 f32)
+# and writes the checkpoint (29) and reward (1); the adjoint reads checkpoint
+# (29), action (8) and reward cotangent (1) and writes the action cotangent (8).
+ALGO_BYTES_PER_ENV_STEP = {"k_batched_forward": 4 * (8 + 29 + 1), "k_batched_adjoint": 4 * (29 + 8 + 1 + 8)}
 
 
 def parse():
@@ -307,8 +321,10 @@ def gpu_main(args, rank, world, dist):
     value = env_steps / (ms_batched * 1e-3)
     plain_value = env_steps / (ms_plain * 1e-3)
     dominant, ms_dom = ("k_batched_adjoint", ms_adj) if ms_adj >= ms_fwd else ("k_batched_forward", ms_fwd)
-    af = ALGO_FLOPS_PER_ENV_STEP["adjoint" if dominant.endswith("adjoint") else "forward"]
+    counts = ALGO_FLOPS_PER_ENV_STEP.get(wl.name)
+    af = counts["adjoint" if dominant.endswith("adjoint") else "forward"] if counts else None
     achieved = None if af is None else af * n_envs * H / (ms_dom * 1e-3) / 1e12
+    traffic = TRAFFIC_BYTES_PER_LAUNCH.get(wl.name, {}).get(dominant)
     line = {
         "metric": METRIC, "value": value, "unit": "env-steps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_batched, "higher_is_better": True, "scaling": "weak",
@@ -330,7 +346,8 @@ def gpu_main(args, rank, world, dist):
         "roofline": {"bound": "alu", "kernel": dominant, "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
                      "unit": "TFLOP/s", "frac": None if achieved is None else achieved / FP32_PEAK_TFLOPS,
                      "peak_source": "derived FP32 peak: 152 SMs x 128 lanes x 2 x 2.07 GHz",
-                     "traffic": None},
+                     "traffic": traffic, "algo_flops_per_env_step": af,
+                     "algo_bytes_per_env_step": ALGO_BYTES_PER_ENV_STEP.get(dominant)},
     }
     if not args.no_cpu_baseline:
         r, n, threads, dt = oracle_window_rate(groups[0][0], groups[0][1], seed=0, target_s=12.0)

@@ -189,6 +189,24 @@ def reference_main(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+# --------------------------------------------------------------- ranks ---
+def shard_seed(rank: int) -> int:
+    """Each rank simulates its own environments (weak scaling): the input
+    seed of a rank's shard."""
+    return rank
+
+
+def max_over_ranks(values, dist, device=None):
+    """Element-wise maximum of per-rank timings (the slowest rank sets the
+    job time); identity without a process group."""
+    if dist is None:
+        return list(values)
+    import torch
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
 # ------------------------------------------------------------------- GPU ---
 def gpu_main(args, rank, world, dist):
     import torch
@@ -206,9 +224,10 @@ def gpu_main(args, rank, world, dist):
         return Simulator(groups, form=form, h_max=H)
 
     sim = make("batched")
-    q0 = sim.pack([I.initial_state(m, n, rank)[0] for m, n in groups], "q")
-    qd0 = sim.pack([I.initial_state(m, n, rank)[1] for m, n in groups], "qd")
-    act = torch.cat([torch.from_numpy(I.window_actions(m, n, H, rank).reshape(H, -1)) for m, n in groups],
+    seed = shard_seed(rank)
+    q0 = sim.pack([I.initial_state(m, n, seed)[0] for m, n in groups], "q")
+    qd0 = sim.pack([I.initial_state(m, n, seed)[1] for m, n in groups], "qd")
+    act = torch.cat([torch.from_numpy(I.window_actions(m, n, H, seed).reshape(H, -1)) for m, n in groups],
                     dim=1).to(dev).contiguous()
     # loss = mean reward over the window: reward cotangent 1 / (N h)
     rbar = torch.full((H, n_envs), 1.0 / (n_envs * H), device=dev)
@@ -311,10 +330,8 @@ def gpu_main(args, rank, world, dist):
     d2h = 4 * (hrew.numel() + hab.numel() + hq0b.numel() + hqd0b.numel())
 
     # max over ranks
-    times = torch.tensor([ms_batched, ms_plain, ms_e2e, ms_fwd, ms_adj], device=dev)
-    if dist is not None:
-        dist.all_reduce(times, op=dist.ReduceOp.MAX)
-    ms_batched, ms_plain, ms_e2e, ms_fwd, ms_adj = times.tolist()
+    ms_batched, ms_plain, ms_e2e, ms_fwd, ms_adj = max_over_ranks([ms_batched, ms_plain, ms_e2e, ms_fwd, ms_adj],
+                                                                  dist, dev)
     if rank != 0:
         return
     env_steps = n_envs * H * world

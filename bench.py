@@ -59,8 +59,8 @@ ALGO_FLOPS_PER_ENV_STEP = {
 # DRAM traffic (read + write) per launch of each batched kernel at h = 32 on
 # ant-2048, scaled from an ncu capture at h = 2 by the 16x env-steps (the
 # per-step traffic is the same at every step); profiles/batched_ant_2048.md.
-# None until captured for the current kernels.
-TRAFFIC_BYTES_PER_LAUNCH = {"ant-2048": {"k_batched_forward": None, "k_batched_adjoint": None}}
+TRAFFIC_BYTES_PER_LAUNCH = {"ant-2048": {"k_batched_forward": 16 * (0.538624e6 + 0.0),
+                                         "k_batched_adjoint": 16 * (13.868544e6 + 113.505024e6)}}
 
 # Algorithmic HBM bytes per env-step (ant): forward reads the action (8 f32)
 # and writes the checkpoint (29) and reward (1); the adjoint reads checkpoint

@@ -1,0 +1,108 @@
+"""Policy in the loop (muscle-actuated lower body, config 5): the actor
+gradient dL/dtheta of an h-step window, computed by PyTorch autograd through
+the library's step adjoint, against the appendix A.1 recursion evaluated with
+the FP64 oracle's step adjoints and a float64 CPU copy of the policy at the
+GPU's states and actions; and CUDA-graph capture of forward + backward."""
+import copy
+
+import numpy as np
+import pytest
+
+from helpers import assert_grad_close
+from paper_2204_07137_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2204_07137_gb300 import build
+    build.build()
+
+
+def T(x):
+    return torch.from_numpy(np.ascontiguousarray(np.asarray(x, np.float32).reshape(-1))).cuda()
+
+
+def _setup(N, h, seed=0):
+    from paper_2204_07137_gb300.policy import PolicyMLP, observation_size
+    from paper_2204_07137_gb300.sim import Simulator
+    m = I.mtu()
+    sim = Simulator([(m, N)], form="batched", h_max=1)
+    g = torch.Generator().manual_seed(seed)
+    pol = PolicyMLP(observation_size(m), m.na, generator=g).cuda()
+    q0, qd0 = I.initial_state(m, N, seed)
+    return m, sim, pol, T(q0), T(qd0)
+
+
+def test_policy_window_gradient_matches_oracle_recursion(oracle_mod):
+    from paper_2204_07137_gb300.policy import free_root_observation, policy_window_loss
+    N, h = 2, 3
+    m, sim, pol, q0, qd0 = _setup(N, h)
+    keep = []
+    loss = policy_window_loss(sim, pol, q0, qd0, h, keep)
+    loss.backward()
+    g_gpu = torch.cat([p.grad.reshape(-1) for p in pol.parameters()]).cpu().numpy()
+    assert np.isfinite(g_gpu).all() and np.abs(g_gpu).max() > 0
+
+    o = oracle_mod.Oracle(m)
+    pol64 = copy.deepcopy(pol).double().cpu()
+    params = list(pol64.parameters())
+    theta_bar = [torch.zeros_like(p) for p in params]
+    qbar = np.zeros((N, m.nq))
+    qdbar = np.zeros((N, m.nv))
+    rbar = np.full(N, -1.0 / (N * h))
+    for t in range(h - 1, -1, -1):
+        q, qd, a = (x.detach().cpu().numpy().astype(np.float64) for x in keep[t])
+        q, qd, a = q.reshape(m.nq, N), qd.reshape(m.nv, N), a.reshape(m.na, N)
+        sq, sqd, sa = o.step_vjp(q.T, qd.T, a.T, qbar, qdbar, rbar)
+        qt = torch.tensor(q, requires_grad=True)
+        qdt = torch.tensor(qd, requires_grad=True)
+        a64 = pol64(free_root_observation(qt, qdt))
+        grads = torch.autograd.grad(a64, [qt, qdt] + params, grad_outputs=torch.tensor(sa))
+        for k, gk in enumerate(grads[2:]):
+            theta_bar[k] += gk
+        qbar = sq + grads[0].numpy().T
+        qdbar = sqd + grads[1].numpy().T
+    g_ref = torch.cat([x.reshape(-1) for x in theta_bar]).numpy()
+    assert_grad_close(g_gpu[:, None], g_ref[:, None], "policy window dL/dtheta", axis_env=-1)
+
+
+def test_policy_window_graph_capture_replays_forward_and_backward():
+    from paper_2204_07137_gb300.policy import policy_window_loss
+    N, h = 4, 3
+    m, sim, pol, q0, qd0 = _setup(N, h, seed=1)
+    params = list(pol.parameters())
+    # eager reference
+    for p in params:
+        p.grad = None
+    loss_ref = policy_window_loss(sim, pol, q0, qd0, h)
+    loss_ref.backward()
+    g_ref = [p.grad.clone() for p in params]
+    # capture the whole window, forward and backward
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        for _ in range(2):   # warm-up on the side stream
+            for p in params:
+                p.grad = None
+            policy_window_loss(sim, pol, q0, qd0, h).backward()
+    torch.cuda.current_stream().wait_stream(s)
+    for p in params:
+        p.grad = None
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        loss_g = policy_window_loss(sim, pol, q0, qd0, h)
+        loss_g.backward()
+    for _ in range(2):
+        for p in params:
+            p.grad.zero_()
+        graph.replay()
+        torch.cuda.synchronize()
+        assert torch.allclose(loss_g, loss_ref, rtol=1e-6, atol=0)
+        for p, g in zip(params, g_ref):
+            assert torch.allclose(p.grad, g, rtol=1e-5, atol=1e-9)

@@ -77,6 +77,8 @@ def parse():
     p.add_argument("--plain-steps", type=int, default=2)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--workload", default=WORKLOAD)
+    p.add_argument("--grad-check-envs", type=int, default=4,
+                   help="sampled environments of the first group checked against the oracle (0: skip)")
     return p.parse_args()
 
 
@@ -138,27 +140,33 @@ class ClockSampler:
 # --------------------------------------------------------------- reference --
 def oracle_window_rate(model, n_envs: int, seed: int = 0, target_s: float = 12.0):
     """env-steps/s of the FP64 oracle (window forward + exact adjoint) on a
-    bounded sample of the workload, sized to about target_s of wall time."""
+    bounded sample of the workload: hs steps of n environments, grown (steps
+    first, up to the 32-step window, then environments) until the sample takes
+    about target_s / 4 .. target_s of wall time."""
     from paper_2204_07137_gb300 import inputs as I
     from oracle import oracle
     o = oracle.Oracle(model)
 
-    def run(n):
+    def run(n, hs):
         q0, qd0 = I.initial_state(model, n, seed)
-        act = I.window_actions(model, n, H, seed)
+        act = I.window_actions(model, n, hs, seed)
         t0 = time.perf_counter()
         qt, qdt, rw = o.window_forward(q0.T, qd0.T, act.transpose(0, 2, 1))
-        o.window_adjoint(qt, qdt, act.transpose(0, 2, 1), np.ones((H, n)), np.zeros((n, model.nq)),
+        o.window_adjoint(qt, qdt, act.transpose(0, 2, 1), np.ones((hs, n)), np.zeros((n, model.nq)),
                          np.zeros((n, model.nv)))
         return time.perf_counter() - t0
 
     threads = oracle.num_threads()
-    n = max(1, min(n_envs, threads))
-    dt = run(n)
-    while dt < target_s / 4 and n < n_envs:
-        n = min(n_envs, max(n + 1, int(n * min(8.0, target_s / max(dt, 1e-3)))))
-        dt = run(n)
-    return n * H / dt, n, threads, dt
+    n, hs = 1, 1
+    dt = run(n, hs)
+    while dt < target_s / 4 and (hs < H or n < n_envs):
+        grow = min(8.0, target_s / max(dt, 1e-3))
+        if hs < H:
+            hs = min(H, max(hs + 1, int(hs * grow)))
+        else:
+            n = min(n_envs, max(n + 1, int(n * grow)))
+        dt = run(n, hs)
+    return n * hs / dt, n, hs, threads, dt
 
 
 def reference_main(args, rank, world):
@@ -172,9 +180,10 @@ def reference_main(args, rank, world):
         pass   # the oracle has no warm-up state; W untimed steps are not needed on the CPU
     samples = []
     for s in range(args.steps):
-        r, n, threads, dt = oracle_window_rate(model, n_total, seed=s, target_s=min(12.0, 60.0 / max(1, args.steps)))
+        r, n, hs, threads, dt = oracle_window_rate(model, n_total, seed=s,
+                                                   target_s=min(12.0, 60.0 / max(1, args.steps)))
         rates.append(r)
-        samples.append((n, dt))
+        samples.append((n, hs, dt))
     value = statistics.median(rates)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "env-steps/s", "n_gpus": args.gpus,
@@ -183,7 +192,7 @@ def reference_main(args, rank, world):
         "config": {"workload": wl.name, "n_envs": n_total, "h": H, "substeps": model.substeps,
                    "form": "FP64 CPU oracle, forward + dual-number exact adjoint"},
         "cpu_baseline": {"value": value, "unit": "env-steps/s", "cores": threads, "kind": "oracle",
-                         "sample": f"{samples[0][0]} of {n_total} envs x {H} steps per timed step"},
+                         "sample": f"{samples[0][0]} of {n_total} envs x {samples[0][1]} steps per timed step"},
         "e2e": {"value": value, "unit": "env-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -289,8 +298,8 @@ def gpu_main(args, rank, world, dist):
 
     # gradient validity gate: sampled environments against the FP64 oracle
     grad_rel = None
-    if rank == 0:
-        grad_rel = gradient_check(sim, groups, outf, outa, act, rbar)
+    if rank == 0 and args.grad_check_envs > 0:
+        grad_rel = gradient_check(sim, groups, outf, outa, act, rbar, n_sample=args.grad_check_envs)
 
     # ---- plain form on the same inputs
     plain = make("plain")
@@ -367,10 +376,10 @@ def gpu_main(args, rank, world, dist):
                      "algo_bytes_per_env_step": ALGO_BYTES_PER_ENV_STEP.get(dominant)},
     }
     if not args.no_cpu_baseline:
-        r, n, threads, dt = oracle_window_rate(groups[0][0], groups[0][1], seed=0, target_s=12.0)
+        r, n, hs, threads, dt = oracle_window_rate(groups[0][0], groups[0][1], seed=0, target_s=12.0)
         line["cpu_baseline"] = {"value": r, "unit": "env-steps/s", "cores": threads, "kind": "oracle",
-                                "sample": f"{n} of {groups[0][1]} envs x {H} steps, forward + exact adjoint, "
-                                          f"{dt:.1f} s"}
+                                "sample": f"{n} of {groups[0][1]} envs ({groups[0][0].name}) x {hs} steps, "
+                                          f"forward + exact adjoint, {dt:.1f} s"}
     print(json.dumps(line), flush=True)
 
 
@@ -383,15 +392,15 @@ def gradient_check(sim, groups, outf, outa, act, rbar, n_sample: int = 4):
     o = oracle.Oracle(model)
     rng = np.random.default_rng(0)
     envs = np.sort(rng.choice(N, size=min(n_sample, N), replace=False))
-    qt = outf[0].cpu().numpy().reshape(H + 1, model.nq, N)[:, :, envs]
-    qdt = outf[1].cpu().numpy().reshape(H + 1, model.nv, N)[:, :, envs]
-    a = act.cpu().numpy().reshape(H, model.na, N)[:, :, envs]
-    rb = rbar.cpu().numpy()[:, envs]
+    qt = sim.unpack(outf[0], "q")[0][:, :, envs]
+    qdt = sim.unpack(outf[1], "qd")[0][:, :, envs]
+    a = sim.unpack(act, "act")[0][:, :, envs]
+    rb = rbar.cpu().numpy()[:, envs]            # group 0 comes first in the reward block
     qb, qdb, ab = o.window_adjoint(qt.transpose(0, 2, 1), qdt.transpose(0, 2, 1), a.transpose(0, 2, 1), rb,
                                    np.zeros((len(envs), model.nq)), np.zeros((len(envs), model.nv)))
-    g_a = outa[2].cpu().numpy().reshape(H, model.na, N)[:, :, envs].transpose(2, 0, 1).reshape(len(envs), -1)
-    g_q = outa[0].cpu().numpy().reshape(model.nq, N)[:, envs].T
-    g_qd = outa[1].cpu().numpy().reshape(model.nv, N)[:, envs].T
+    g_a = sim.unpack(outa[2], "act")[0][:, :, envs].transpose(2, 0, 1).reshape(len(envs), -1)
+    g_q = sim.unpack(outa[0], "q")[0][:, envs].T
+    g_qd = sim.unpack(outa[1], "qd")[0][:, envs].T
     got = np.concatenate([g_a, g_q, g_qd], axis=1)
     ref = np.concatenate([ab.transpose(1, 0, 2).reshape(len(envs), -1), qb, qdb], axis=1)
     rel = np.linalg.norm(got - ref, axis=1) / np.linalg.norm(ref, axis=1)

@@ -16,7 +16,7 @@ struct shac_model {
   float h = 0, grav[3] = {0, 0, 0}, ke = 0, kd = 0, kt = 0, mu = 0, klim = 0, rc[10] = {0};
   int root_free = 0;
   std::vector<int> parent, jtype, qs, ds, nd, lvl_ptr, lvl_link, ch_ptr, ch_idx, li_ptr, li_idx, dof_link, dof_k,
-      dof_act, item_link, seg_mus, mus_seg_ptr, anc_mask;
+      dof_act, item_link, seg_mus, mus_seg_ptr, anc_mask, chain_tail;
   std::vector<float> axis, jpos, jrot, mass, com, icom, qlo, qhi, arm, damp, gear, item_pos, crad, fmax, rwq, rwqd;
   DevModel layout;   // sizes + scratch offsets (pointers unset)
 };
@@ -129,21 +129,7 @@ extern "C" shac_status shac_model_create(const shac_model_desc* dsc, shac_model*
     for (int k = 0; k < 3; ++k) m->com.push_back(dsc->com[3 * i + k]);
     for (int k = 0; k < 6; ++k) m->icom.push_back(dsc->inertia[6 * i + k]);
   }
-  // depth levels
-  std::vector<int> depth(L, 0);
-  int maxd = 0;
-  for (int i = 0; i < L; ++i) {
-    depth[i] = m->parent[i] < 0 ? 0 : depth[m->parent[i]] + 1;
-    maxd = std::max(maxd, depth[i]);
-  }
-  m->nlev = maxd + 1;
-  m->lvl_ptr.assign(m->nlev + 1, 0);
-  for (int l = 0; l < m->nlev; ++l) {
-    m->lvl_ptr[l] = (int)m->lvl_link.size();
-    for (int i = 0; i < L; ++i)
-      if (depth[i] == l) m->lvl_link.push_back(i);
-  }
-  m->lvl_ptr[m->nlev] = L;
+  // children lists
   m->ch_ptr.assign(L + 1, 0);
   for (int i = 0; i < L; ++i) {
     m->ch_ptr[i] = (int)m->ch_idx.size();
@@ -151,6 +137,28 @@ extern "C" shac_status shac_model_create(const shac_model_desc* dsc, shac_model*
       if (m->parent[c] == i) m->ch_idx.push_back(c);
   }
   m->ch_ptr[L] = (int)m->ch_idx.size();
+  // Chains: maximal runs of links in which every link but the last has exactly
+  // one child; a chain is swept by one lane (parent before child), so tree
+  // sweeps need one team barrier per chain level instead of per link depth.
+  std::vector<int> head(L), cdepth(L, 0);
+  m->chain_tail.assign(L, -1);
+  int maxd = 0;
+  for (int i = 0; i < L; ++i) {
+    const int p = m->parent[i];
+    const bool cont = p >= 0 && m->ch_ptr[p + 1] - m->ch_ptr[p] == 1;
+    head[i] = cont ? head[p] : i;
+    cdepth[i] = p < 0 ? 0 : (cont ? cdepth[p] : cdepth[p] + 1);
+    maxd = std::max(maxd, cdepth[i]);
+  }
+  for (int i = 0; i < L; ++i) m->chain_tail[head[i]] = i;   // links are numbered parent first
+  m->nlev = maxd + 1;
+  m->lvl_ptr.assign(m->nlev + 1, 0);
+  for (int l = 0; l < m->nlev; ++l) {
+    m->lvl_ptr[l] = (int)m->lvl_link.size();
+    for (int i = 0; i < L; ++i)
+      if (head[i] == i && cdepth[i] == l) m->lvl_link.push_back(i);
+  }
+  m->lvl_ptr[m->nlev] = (int)m->lvl_link.size();
   // dofs
   for (int i = 0; i < L; ++i)
     for (int k = 0; k < m->nd[i]; ++k) { m->dof_link.push_back(i); m->dof_k.push_back(k); }
@@ -262,7 +270,7 @@ static shac_status upload_model(const shac_model* m, Group& g) {
     fblob.push_back(0.f);
   };
   addi(&d.parent, m->parent); addi(&d.jtype, m->jtype); addi(&d.qs, m->qs); addi(&d.ds, m->ds); addi(&d.nd, m->nd);
-  addi(&d.lvl_ptr, m->lvl_ptr); addi(&d.lvl_link, m->lvl_link); addi(&d.ch_ptr, m->ch_ptr); addi(&d.ch_idx, m->ch_idx);
+  addi(&d.lvl_ptr, m->lvl_ptr); addi(&d.lvl_link, m->lvl_link); addi(&d.chain_tail, m->chain_tail); addi(&d.ch_ptr, m->ch_ptr); addi(&d.ch_idx, m->ch_idx);
   addi(&d.li_ptr, m->li_ptr); addi(&d.li_idx, m->li_idx); addi(&d.dof_link, m->dof_link); addi(&d.dof_k, m->dof_k);
   addi(&d.dof_act, m->dof_act); addi(&d.item_link, m->item_link); addi(&d.seg_mus, m->seg_mus);
   addi(&d.mus_seg_ptr, m->mus_seg_ptr);

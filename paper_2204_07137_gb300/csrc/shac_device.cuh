@@ -54,7 +54,8 @@ struct DevModel {
   int root_free;                         // link 0 is a free joint
   // links
   const int *parent, *jtype, *qs, *ds, *nd;
-  const int *lvl_ptr, *lvl_link;         // links grouped by depth
+  const int *lvl_ptr, *lvl_link;         // chain heads grouped by chain depth
+  const int *chain_tail;                 // last link of the chain starting at a head
   const int *ch_ptr, *ch_idx;            // children lists
   const int *li_ptr, *li_idx;            // force items attached to each link
   const float *axis, *jpos, *jrot, *mass, *com, *icom;
@@ -205,82 +206,12 @@ __device__ __forceinline__ void si_mul(const Mem& w, int o, V3 xw, V3 xv, V3& yn
 // level.  A forward substep is two sweeps plus the dense solve; the plain
 // form calls the same functions from one thread per environment.
 
-// Forward kinematics of link i from its parent: rotation R_i, origin P_i.
-template <class Mem>
-__device__ __forceinline__ void lk_fk(const DevModel& M, const Mem& w, int i) {
-  const int jt = __ldg(M.jtype + i), s = __ldg(M.qs + i), p = __ldg(M.parent + i);
-  M33 R;
-  V3 P;
-  if (jt == J_FREE) {
-    // Spatial quantities use the free root's origin as reference point
-    // (translation invariance); only contact depths need its height back.
-    R = quat_to_R(w[M.o_Q + s + 3], w[M.o_Q + s + 4], w[M.o_Q + s + 5], w[M.o_Q + s + 6]);
-    P = v3(0.f, 0.f, 0.f);
-  } else {
-    M33 Rj = cldm(M.jrot + 9 * i);
-    V3 Pj = cld3(M.jpos + 3 * i);
-    if (p >= 0) {
-      M33 Rp = ldm(w, M.o_R + 9 * p);
-      Pj = ld3(w, M.o_P + 3 * p) + mul(Rp, Pj);
-      Rj = mul(Rp, Rj);
-    }
-    if (jt == J_REV) {
-      R = mul(Rj, axis_angle(cld3(M.axis + 3 * i), w[M.o_Q + s]));
-      P = Pj;
-    } else if (jt == J_PRIS) {
-      R = Rj;
-      P = Pj + w[M.o_Q + s] * mul(Rj, cld3(M.axis + 3 * i));
-    } else {
-      R = Rj;
-      P = Pj;
-    }
-  }
-  stm(w, M.o_R + 9 * i, R);
-  st3(w, M.o_P + 3 * i, P);
-}
-
 __device__ __forceinline__ M33 com_inertia(const DevModel& M, int i) {
   const float* ic = M.icom + 6 * i;
   M33 Ic;
   Ic.m[0] = __ldg(ic); Ic.m[4] = __ldg(ic + 1); Ic.m[8] = __ldg(ic + 2);
   Ic.m[1] = Ic.m[3] = __ldg(ic + 3); Ic.m[2] = Ic.m[6] = __ldg(ic + 4); Ic.m[5] = Ic.m[7] = __ldg(ic + 5);
   return Ic;
-}
-
-// Spatial inertia of link i at the reference point (m, h = m c, Io) and the
-// motion-subspace columns of its DOFs: revolute (a, P x a), prismatic (0, a),
-// free (R e_k, P x R e_k) for the body angular rates, (0, R e_k) for v_body.
-template <class Mem>
-__device__ __forceinline__ void lk_quant(const DevModel& M, const Mem& w, int i) {
-  const M33 R = ldm(w, M.o_R + 9 * i);
-  const V3 P = ld3(w, M.o_P + 3 * i);
-  const float m = __ldg(M.mass + i);
-  const V3 c = P + mul(R, cld3(M.com + 3 * i));
-  const M33 Iw = mulBT(mul(R, com_inertia(M, i)), R);
-  const float cc = dot(c, c);
-  const int o = M.o_SI + 10 * i;
-  w[o] = m;
-  st3(w, o + 1, m * c);
-  w[o + 4] = Iw.m[0] + m * (cc - c.x * c.x);
-  w[o + 5] = Iw.m[4] + m * (cc - c.y * c.y);
-  w[o + 6] = Iw.m[8] + m * (cc - c.z * c.z);
-  w[o + 7] = Iw.m[1] - m * c.x * c.y;
-  w[o + 8] = Iw.m[2] - m * c.x * c.z;
-  w[o + 9] = Iw.m[5] - m * c.y * c.z;
-  const int jt = __ldg(M.jtype + i), d0 = __ldg(M.ds + i), nd = __ldg(M.nd + i);
-  for (int k = 0; k < nd; ++k) {
-    V3 sw, sv;
-    if (jt == J_FREE) {
-      if (k < 3) { sw = col(R, k); sv = cross(P, sw); }
-      else { sw = v3(0.f, 0.f, 0.f); sv = col(R, k - 3); }
-    } else {
-      const V3 a = mul(R, cld3(M.axis + 3 * i));
-      if (jt == J_REV) { sw = a; sv = cross(P, a); }
-      else { sw = v3(0.f, 0.f, 0.f); sv = a; }
-    }
-    st3(w, M.o_S + 6 * (d0 + k), sw);
-    st3(w, M.o_S + 6 * (d0 + k) + 3, sv);
-  }
 }
 
 // joint spatial velocity u_i = sum_{d in i} S_d qd_d
@@ -292,80 +223,6 @@ __device__ __forceinline__ void joint_vel(const DevModel& M, const Mem& w, int i
     const float qd = w[M.o_QD + d];
     uw = uw + qd * ld3(w, M.o_S + 6 * d);
     uv = uv + qd * ld3(w, M.o_S + 6 * d + 3);
-  }
-}
-
-// V_i = V_parent + u_i
-template <class Mem>
-__device__ __forceinline__ void lk_vel(const DevModel& M, const Mem& w, int i) {
-  const int p = __ldg(M.parent + i);
-  V3 uw, uv;
-  joint_vel(M, w, i, uw, uv);
-  if (p >= 0) { uw = uw + ld3(w, M.o_V + 6 * p); uv = uv + ld3(w, M.o_V + 6 * p + 3); }
-  st3(w, M.o_V + 6 * i, uw);
-  st3(w, M.o_V + 6 * i + 3, uv);
-}
-
-// Newton-Euler acceleration A_i = A_parent + sum_d S_d qdd_d + V_i x u_i,
-// gravity entering as the base acceleration -g (qdd = 0 for the bias C).
-template <class Mem>
-__device__ __forceinline__ void lk_acc(const DevModel& M, const Mem& w, int i, bool use_qdd) {
-  const int p = __ldg(M.parent + i);
-  V3 aw, av;
-  if (p >= 0) { aw = ld3(w, M.o_A + 6 * p); av = ld3(w, M.o_A + 6 * p + 3); }
-  else { aw = v3(0.f, 0.f, 0.f); av = v3(-M.grav[0], -M.grav[1], -M.grav[2]); }
-  V3 uw, uv;
-  joint_vel(M, w, i, uw, uv);
-  const V3 Vw = ld3(w, M.o_V + 6 * i), Vv = ld3(w, M.o_V + 6 * i + 3);
-  aw = aw + cross(Vw, uw);
-  av = av + cross(Vw, uv) + cross(Vv, uw);
-  if (use_qdd) {
-    const int d0 = __ldg(M.ds + i), n = __ldg(M.nd + i);
-    for (int d = d0; d < d0 + n; ++d) {
-      const float a = w[M.o_QDD + d];
-      aw = aw + a * ld3(w, M.o_S + 6 * d);
-      av = av + a * ld3(w, M.o_S + 6 * d + 3);
-    }
-  }
-  st3(w, M.o_A + 6 * i, aw);
-  st3(w, M.o_A + 6 * i + 3, av);
-}
-
-// Sec. 3.1 contact model on the ground plane z = 0 (n = +z) for the contact
-// spheres of link i, applied at the lowest point x of each sphere:
-//   f_n = (-ke + kd ddot) min(d, 0),  d = height of x, ddot = v_x . n
-//   f_t = -v_t/|v_t| min(kt |v_t|, mu |f_n|)  (viscous branch when kt|v_t| <= mu|f_n|)
-// Stores (x, f, d) per contact and returns the wrench sum (x cross f, f).
-template <class Mem>
-__device__ __forceinline__ void lk_contacts(const DevModel& M, const Mem& w, int i, V3& wn, V3& wf) {
-  wn = v3(0.f, 0.f, 0.f); wf = v3(0.f, 0.f, 0.f);
-  const int k0 = __ldg(M.li_ptr + i), k1 = __ldg(M.li_ptr + i + 1);
-  if (k0 == k1) return;
-  const M33 R = ldm(w, M.o_R + 9 * i);
-  const V3 P = ld3(w, M.o_P + 3 * i);
-  const V3 Vw = ld3(w, M.o_V + 6 * i), Vv = ld3(w, M.o_V + 6 * i + 3);
-  const float zroot = M.root_free ? w[M.o_Q + 2] : 0.f;
-  for (int k = k0; k < k1; ++k) {
-    const int c = __ldg(M.li_idx + k);
-    if (c >= M.nc) continue;   // muscle via point
-    V3 x = P + mul(R, cld3(M.item_pos + 3 * c));
-    x.z -= __ldg(M.crad + c);
-    const float d = x.z + zroot;   // height above the plane
-    V3 f = v3(0.f, 0.f, 0.f);
-    if (d < 0.f) {
-      const V3 vp = Vv + cross(Vw, x);
-      const float fn = (-M.ke + M.kd * vp.z) * d;
-      const float vt = sqrtf(vp.x * vp.x + vp.y * vp.y);
-      const float afn = fabsf(fn);
-      if (M.kt * vt <= M.mu * afn) { f.x = -M.kt * vp.x; f.y = -M.kt * vp.y; }
-      else { const float sc = M.mu * afn / vt; f.x = -sc * vp.x; f.y = -sc * vp.y; }
-      f.z = fn;
-    }
-    st3(w, M.o_IT + 7 * c, x);
-    st3(w, M.o_IT + 7 * c + 3, f);
-    w[M.o_IT + 7 * c + 6] = d;
-    wn = wn + cross(x, f);
-    wf = wf + f;
   }
 }
 
@@ -401,16 +258,132 @@ __device__ __forceinline__ void lk_muscle_wrench(const DevModel& M, const Mem& w
   }
 }
 
-// local force F_i = I_i A_i + V_i x* (I_i V_i) - Fext_i
+// Tree sweeps visit chains: maximal runs of links in which every link but the
+// last has exactly one child.  A lane walks its chain parent-first (root-first
+// sweeps) or child-first (leaves-first sweeps); one team barrier per chain level.
+__device__ __forceinline__ int chain_next(const DevModel& M, int i) { return __ldg(M.ch_idx + __ldg(M.ch_ptr + i)); }
+
+// All of sweep 1's work for link i in one pass, values kept in registers:
+// forward kinematics from the parent (rotation R_i, origin P_i), the spatial
+// inertia about the reference point (m, h = m c, Io), the motion-subspace
+// columns (revolute (a, P x a), prismatic (0, a), free (R e_k, P x R e_k) for
+// the body rates and (0, R e_k) for v_body), the velocity V_i = V_p + u_i, the
+// Newton-Euler acceleration A_i = A_p + V_i x u_i with qdd = 0 (gravity enters
+// as the base acceleration -g), the contact forces and the local force
+// F_i = I_i A_i + V_i x* (I_i V_i) - Fext_i.
 template <class Mem>
-__device__ __forceinline__ void lk_force(const DevModel& M, const Mem& w, int i) {
-  const V3 aw = ld3(w, M.o_A + 6 * i), av = ld3(w, M.o_A + 6 * i + 3);
-  const V3 Vw = ld3(w, M.o_V + 6 * i), Vv = ld3(w, M.o_V + 6 * i + 3);
+__device__ __forceinline__ void lk_forward(const DevModel& M, const Mem& w, int i) {
+  const int jt = __ldg(M.jtype + i), s = __ldg(M.qs + i), p = __ldg(M.parent + i);
+  const int d0 = __ldg(M.ds + i), nd = __ldg(M.nd + i);
+  // kinematics
+  M33 R;
+  V3 P;
+  const V3 ax = cld3(M.axis + 3 * i);
+  if (jt == J_FREE) {
+    R = quat_to_R(w[M.o_Q + s + 3], w[M.o_Q + s + 4], w[M.o_Q + s + 5], w[M.o_Q + s + 6]);
+    P = v3(0.f, 0.f, 0.f);
+  } else {
+    M33 Rj = cldm(M.jrot + 9 * i);
+    V3 Pj = cld3(M.jpos + 3 * i);
+    if (p >= 0) {
+      const M33 Rp = ldm(w, M.o_R + 9 * p);
+      Pj = ld3(w, M.o_P + 3 * p) + mul(Rp, Pj);
+      Rj = mul(Rp, Rj);
+    }
+    if (jt == J_REV) { R = mul(Rj, axis_angle(ax, w[M.o_Q + s])); P = Pj; }
+    else if (jt == J_PRIS) { R = Rj; P = Pj + w[M.o_Q + s] * mul(Rj, ax); }
+    else { R = Rj; P = Pj; }
+  }
+  stm(w, M.o_R + 9 * i, R);
+  st3(w, M.o_P + 3 * i, P);
+  // spatial inertia about the reference point
+  const float m = __ldg(M.mass + i);
+  const V3 c = P + mul(R, cld3(M.com + 3 * i));
+  const M33 Iw = mulBT(mul(R, com_inertia(M, i)), R);
+  const float cc = dot(c, c);
+  const V3 h = m * c;
+  const float ixx = Iw.m[0] + m * (cc - c.x * c.x), iyy = Iw.m[4] + m * (cc - c.y * c.y);
+  const float izz = Iw.m[8] + m * (cc - c.z * c.z), ixy = Iw.m[1] - m * c.x * c.y;
+  const float ixz = Iw.m[2] - m * c.x * c.z, iyz = Iw.m[5] - m * c.y * c.z;
+  {
+    const int o = M.o_SI + 10 * i;
+    w[o] = m; st3(w, o + 1, h);
+    w[o + 4] = ixx; w[o + 5] = iyy; w[o + 6] = izz; w[o + 7] = ixy; w[o + 8] = ixz; w[o + 9] = iyz;
+  }
+  auto imul = [&](V3 xw, V3 xv, V3& yn, V3& yf) {
+    yn = v3(ixx * xw.x + ixy * xw.y + ixz * xw.z, ixy * xw.x + iyy * xw.y + iyz * xw.z,
+            ixz * xw.x + iyz * xw.y + izz * xw.z) + cross(h, xv);
+    yf = m * xv - cross(h, xw);
+  };
+  // motion subspaces and joint velocity u = sum S qd
+  V3 uw = v3(0.f, 0.f, 0.f), uv = v3(0.f, 0.f, 0.f);
+  for (int k = 0; k < nd; ++k) {
+    V3 sw, sv;
+    if (jt == J_FREE) {
+      if (k < 3) { sw = col(R, k); sv = cross(P, sw); }
+      else { sw = v3(0.f, 0.f, 0.f); sv = col(R, k - 3); }
+    } else {
+      const V3 a = mul(R, ax);
+      if (jt == J_REV) { sw = a; sv = cross(P, a); }
+      else { sw = v3(0.f, 0.f, 0.f); sv = a; }
+    }
+    st3(w, M.o_S + 6 * (d0 + k), sw);
+    st3(w, M.o_S + 6 * (d0 + k) + 3, sv);
+    const float qd = w[M.o_QD + d0 + k];
+    uw = uw + qd * sw;
+    uv = uv + qd * sv;
+  }
+  // velocity and acceleration (qdd = 0; gravity as base acceleration)
+  V3 Vw = uw, Vv = uv, aw, av;
+  if (p >= 0) {
+    Vw = Vw + ld3(w, M.o_V + 6 * p); Vv = Vv + ld3(w, M.o_V + 6 * p + 3);
+    aw = ld3(w, M.o_A + 6 * p); av = ld3(w, M.o_A + 6 * p + 3);
+  } else {
+    aw = v3(0.f, 0.f, 0.f); av = v3(-M.grav[0], -M.grav[1], -M.grav[2]);
+  }
+  aw = aw + cross(Vw, uw);
+  av = av + cross(Vw, uv) + cross(Vv, uw);
+  st3(w, M.o_V + 6 * i, Vw); st3(w, M.o_V + 6 * i + 3, Vv);
+  st3(w, M.o_A + 6 * i, aw); st3(w, M.o_A + 6 * i + 3, av);
+  // Sec. 3.1 contact model on the ground plane z = 0 (n = +z) for the contact
+  // spheres of link i, applied at the lowest point x of each sphere:
+  //   f_n = (-ke + kd ddot) min(d, 0),  d = height of x, ddot = v_x . n
+  //   f_t = -v_t/|v_t| min(kt |v_t|, mu |f_n|)  (viscous branch when kt|v_t| <= mu|f_n|)
+  V3 wn = v3(0.f, 0.f, 0.f), wf = v3(0.f, 0.f, 0.f);
+  const int k0 = __ldg(M.li_ptr + i), k1 = __ldg(M.li_ptr + i + 1);
+  if (k0 != k1) {
+    const float zroot = M.root_free ? w[M.o_Q + 2] : 0.f;
+    for (int k = k0; k < k1; ++k) {
+      const int ci = __ldg(M.li_idx + k);
+      if (ci >= M.nc) continue;   // muscle via point
+      V3 x = P + mul(R, cld3(M.item_pos + 3 * ci));
+      x.z -= __ldg(M.crad + ci);
+      const float d = x.z + zroot;
+      V3 f = v3(0.f, 0.f, 0.f);
+      if (d < 0.f) {
+        const V3 vp = Vv + cross(Vw, x);
+        const float fn = (-M.ke + M.kd * vp.z) * d;
+        const float vt = sqrtf(vp.x * vp.x + vp.y * vp.y);
+        const float afn = fabsf(fn);
+        if (M.kt * vt <= M.mu * afn) { f.x = -M.kt * vp.x; f.y = -M.kt * vp.y; }
+        else { const float sc = M.mu * afn / vt; f.x = -sc * vp.x; f.y = -sc * vp.y; }
+        f.z = fn;
+      }
+      st3(w, M.o_IT + 7 * ci, x);
+      st3(w, M.o_IT + 7 * ci + 3, f);
+      w[M.o_IT + 7 * ci + 6] = d;
+      wn = wn + cross(x, f);
+      wf = wf + f;
+    }
+  }
+  st3(w, M.o_FX + 6 * i, wn);
+  st3(w, M.o_FX + 6 * i + 3, wf);
+  // local force F = I A + V x* (I V) - Fext
   V3 fn, ff, bn, bf;
-  si_mul(w, M.o_SI + 10 * i, aw, av, fn, ff);
-  si_mul(w, M.o_SI + 10 * i, Vw, Vv, bn, bf);
-  fn = fn + cross(Vw, bn) + cross(Vv, bf) - ld3(w, M.o_FX + 6 * i);
-  ff = ff + cross(Vw, bf) - ld3(w, M.o_FX + 6 * i + 3);
+  imul(aw, av, fn, ff);
+  imul(Vw, Vv, bn, bf);
+  fn = fn + cross(Vw, bn) + cross(Vv, bf) - wn;
+  ff = ff + cross(Vw, bf) - wf;
   st3(w, M.o_F + 6 * i, fn);
   st3(w, M.o_F + 6 * i + 3, ff);
 }
@@ -422,16 +395,11 @@ template <class Mem>
 __device__ void sw_forward(const DevModel& M, const Mem& w, int lane, int nl) {
   for (int l = 0; l < M.nlev; ++l) {
     for (int ii = __ldg(M.lvl_ptr + l) + lane; ii < __ldg(M.lvl_ptr + l + 1); ii += nl) {
-      const int i = __ldg(M.lvl_link + ii);
-      lk_fk(M, w, i);
-      lk_quant(M, w, i);
-      lk_vel(M, w, i);
-      lk_acc(M, w, i, false);
-      V3 wn, wf;
-      lk_contacts(M, w, i, wn, wf);
-      st3(w, M.o_FX + 6 * i, wn);
-      st3(w, M.o_FX + 6 * i + 3, wf);
-      lk_force(M, w, i);
+      const int hd = __ldg(M.lvl_link + ii), tl = __ldg(M.chain_tail + hd);
+      for (int i = hd;; i = chain_next(M, i)) {
+        lk_forward(M, w, i);
+        if (i == tl) break;
+      }
     }
     team_sync(nl);
   }
@@ -482,8 +450,13 @@ __device__ __forceinline__ void lk_gather(const DevModel& M, const Mem& w, int i
 template <class Mem>
 __device__ void sw_gather(const DevModel& M, const Mem& w, int lane, int nl, bool with_ic) {
   for (int l = M.nlev - 1; l >= 0; --l) {
-    for (int ii = __ldg(M.lvl_ptr + l) + lane; ii < __ldg(M.lvl_ptr + l + 1); ii += nl)
-      lk_gather(M, w, __ldg(M.lvl_link + ii), with_ic);
+    for (int ii = __ldg(M.lvl_ptr + l) + lane; ii < __ldg(M.lvl_ptr + l + 1); ii += nl) {
+      const int hd = __ldg(M.lvl_link + ii);
+      for (int i = __ldg(M.chain_tail + hd);; i = __ldg(M.parent + i)) {
+        lk_gather(M, w, i, with_ic);
+        if (i == hd) break;
+      }
+    }
     team_sync(nl);
   }
 }
@@ -886,15 +859,35 @@ __device__ __forceinline__ void lk_adj_fwd(const DevModel& M, const Mem& w, int 
 #pragma unroll
   for (int k = 0; k < 9; ++k) w[M.o_RB + 9 * i + k] = 0.f;
   w[M.o_PB + 3 * i] = 0.f; w[M.o_PB + 3 * i + 1] = 0.f; w[M.o_PB + 3 * i + 2] = 0.f;
-  lk_acc(M, w, i, true);
-  lk_force(M, w, i);
   const int p = __ldg(M.parent + i), d0 = __ldg(M.ds + i), nd = __ldg(M.nd + i), jt = __ldg(M.jtype + i);
-  V3 nb = v3(0.f, 0.f, 0.f), fb = v3(0.f, 0.f, 0.f);
-  if (p >= 0) { nb = ld3(w, M.o_FB + 6 * p); fb = ld3(w, M.o_FB + 6 * p + 3); }
+  const int osi = M.o_SI + 10 * i, osb = M.o_SIB + 12 * i;
+  // spatial inertia in registers
+  const float m = w[osi];
+  const V3 h = ld3(w, osi + 1);
+  const float ixx = w[osi + 4], iyy = w[osi + 5], izz = w[osi + 6], ixy = w[osi + 7], ixz = w[osi + 8],
+              iyz = w[osi + 9];
+  auto imul = [&](V3 xw, V3 xv, V3& yn, V3& yf) {
+    yn = v3(ixx * xw.x + ixy * xw.y + ixz * xw.z, ixy * xw.x + iyy * xw.y + iyz * xw.z,
+            ixz * xw.x + iyz * xw.y + izz * xw.z) + cross(h, xv);
+    yf = m * xv - cross(h, xw);
+  };
+  const V3 Vw = ld3(w, M.o_V + 6 * i), Vv = ld3(w, M.o_V + 6 * i + 3);
+  // accelerations with the solved qdd, local force F = I A + V x* (I V) - Fext,
+  // and the force cotangent F_bar = sum_{d in i} (-lambda_d) S_d + F_bar_parent
+  V3 aw, av, nb = v3(0.f, 0.f, 0.f), fb = v3(0.f, 0.f, 0.f);
+  if (p >= 0) {
+    aw = ld3(w, M.o_A + 6 * p); av = ld3(w, M.o_A + 6 * p + 3);
+    nb = ld3(w, M.o_FB + 6 * p); fb = ld3(w, M.o_FB + 6 * p + 3);
+  } else {
+    aw = v3(0.f, 0.f, 0.f); av = v3(-M.grav[0], -M.grav[1], -M.grav[2]);
+  }
+  V3 uw = v3(0.f, 0.f, 0.f), uv = v3(0.f, 0.f, 0.f);
   for (int d = d0; d < d0 + nd; ++d) {
-    const float lam = w[M.o_LAM + d];
-    nb = nb - lam * ld3(w, M.o_S + 6 * d);
-    fb = fb - lam * ld3(w, M.o_S + 6 * d + 3);
+    const V3 sw = ld3(w, M.o_S + 6 * d), sv = ld3(w, M.o_S + 6 * d + 3);
+    const float qd = w[M.o_QD + d], qdd = w[M.o_QDD + d], lam = w[M.o_LAM + d];
+    uw = uw + qd * sw; uv = uv + qd * sv;
+    aw = aw + qdd * sw; av = av + qdd * sv;
+    nb = nb - lam * sw; fb = fb - lam * sv;
     // joint forces: tau_j_bar = lambda
     const int a = __ldg(M.dof_act + d);
     if (a >= 0) w[M.o_ACTB + a] += lam * __ldg(M.gear + d);
@@ -905,26 +898,34 @@ __device__ __forceinline__ void lk_adj_fwd(const DevModel& M, const Mem& w, int 
     }
     w[M.o_QDB + d] -= lam * __ldg(M.damp + d);
   }
+  aw = aw + cross(Vw, uw);
+  av = av + cross(Vw, uv) + cross(Vv, uw);
+  st3(w, M.o_A + 6 * i, aw); st3(w, M.o_A + 6 * i + 3, av);
+  {
+    V3 fn, ff, bn, bf;
+    imul(aw, av, fn, ff);
+    imul(Vw, Vv, bn, bf);
+    fn = fn + cross(Vw, bn) + cross(Vv, bf) - ld3(w, M.o_FX + 6 * i);
+    ff = ff + cross(Vw, bf) - ld3(w, M.o_FX + 6 * i + 3);
+    st3(w, M.o_F + 6 * i, fn); st3(w, M.o_F + 6 * i + 3, ff);
+  }
   st3(w, M.o_FB + 6 * i, nb);
   st3(w, M.o_FB + 6 * i + 3, fb);
-  const V3 aw = ld3(w, M.o_A + 6 * i), av = ld3(w, M.o_A + 6 * i + 3);
-  const V3 Vw = ld3(w, M.o_V + 6 * i), Vv = ld3(w, M.o_V + 6 * i + 3);
-  const int osi = M.o_SI + 10 * i, osb = M.o_SIB + 12 * i;
   // A_bar = I F_bar (I symmetric)
   V3 abn, abf;
-  si_mul(w, osi, nb, fb, abn, abf);
+  imul(nb, fb, abn, abf);
   st3(w, M.o_AB + 6 * i, abn);
   st3(w, M.o_AB + 6 * i + 3, abf);
   si_mul_adj(w, osb, aw, av, nb, fb);
   // momentum B = I V and V x* B
   V3 Bn, Bf;
-  si_mul(w, osi, Vw, Vv, Bn, Bf);
+  imul(Vw, Vv, Bn, Bf);
   V3 vwb = cross(Bn, nb) + cross(Bf, fb);
   V3 vvb = cross(Bf, nb);
   const V3 Bnb = cross(nb, Vw);
   const V3 Bfb = cross(nb, Vv) + cross(fb, Vw);
   V3 t1, t2;
-  si_mul(w, osi, Bnb, Bfb, t1, t2);
+  imul(Bnb, Bfb, t1, t2);
   vwb = vwb + t1;
   vvb = vvb + t2;
   si_mul_adj(w, osb, Vw, Vv, Bnb, Bfb);
@@ -1165,8 +1166,13 @@ __device__ void st_dynamics_adj(const DevModel& M, const Mem& w, int lane, int n
     st_solve(M, w, lane, nl, M.o_B, M.o_LAM);
   }
   for (int l = 0; l < M.nlev; ++l) {
-    for (int ii = __ldg(M.lvl_ptr + l) + lane; ii < __ldg(M.lvl_ptr + l + 1); ii += nl)
-      lk_adj_fwd(M, w, __ldg(M.lvl_link + ii));
+    for (int ii = __ldg(M.lvl_ptr + l) + lane; ii < __ldg(M.lvl_ptr + l + 1); ii += nl) {
+      const int hd = __ldg(M.lvl_link + ii), tl = __ldg(M.chain_tail + hd);
+      for (int i = hd;; i = chain_next(M, i)) {
+        lk_adj_fwd(M, w, i);
+        if (i == tl) break;
+      }
+    }
     team_sync(nl);
   }
   if (M.nseg > 0) {
@@ -1196,8 +1202,13 @@ __device__ void st_dynamics_adj(const DevModel& M, const Mem& w, int lane, int n
     team_sync(nl);
   }
   for (int l = M.nlev - 1; l >= 0; --l) {
-    for (int ii = __ldg(M.lvl_ptr + l) + lane; ii < __ldg(M.lvl_ptr + l + 1); ii += nl)
-      lk_adj_bwd(M, w, __ldg(M.lvl_link + ii));
+    for (int ii = __ldg(M.lvl_ptr + l) + lane; ii < __ldg(M.lvl_ptr + l + 1); ii += nl) {
+      const int hd = __ldg(M.lvl_link + ii);
+      for (int i = __ldg(M.chain_tail + hd);; i = __ldg(M.parent + i)) {
+        lk_adj_bwd(M, w, i);
+        if (i == hd) break;
+      }
+    }
     team_sync(nl);
   }
 }

@@ -184,8 +184,10 @@ class SimStep(torch.autograd.Function):
     @staticmethod
     def forward(ctx, sim: Simulator, q, qd, act):
         q, qd, act = q.contiguous(), qd.contiguous(), act.contiguous()
-        qn, qdn, r = sim.step(q, qd, act)
+        stream = torch.cuda.current_stream(sim.device)
+        qn, qdn, r = sim.step(q, qd, act, stream=stream)
         ctx.sim = sim
+        ctx.stream = stream
         ctx.save_for_backward(q, qd, act)
         return qn, qdn, r
 
@@ -193,8 +195,11 @@ class SimStep(torch.autograd.Function):
     def backward(ctx, gq, gqd, gr):
         sim = ctx.sim
         q, qd, act = ctx.saved_tensors
-        z = lambda n, g: torch.zeros(n, device=sim.device) if g is None else g.contiguous()
-        qb, qdb, ab = sim.step_adjoint(q, qd, act, z(sim.q_size, gq), z(sim.qd_size, gqd), z(sim.n_envs, gr))
+        # the adjoint runs on the forward's stream (also inside a graph capture)
+        with torch.cuda.stream(ctx.stream):
+            z = lambda n, g: torch.zeros(n, device=sim.device) if g is None else g.contiguous()
+            qb, qdb, ab = sim.step_adjoint(q, qd, act, z(sim.q_size, gq), z(sim.qd_size, gqd), z(sim.n_envs, gr),
+                                           stream=ctx.stream)
         return None, qb, qdb, ab
 
 
@@ -205,8 +210,10 @@ class SimWindow(torch.autograd.Function):
     @staticmethod
     def forward(ctx, sim: Simulator, q0, qd0, act):
         q0, qd0, act = q0.contiguous(), qd0.contiguous(), act.contiguous()
-        q_traj, qd_traj, rew = sim.window_forward(q0, qd0, act)
+        stream = torch.cuda.current_stream(sim.device)
+        q_traj, qd_traj, rew = sim.window_forward(q0, qd0, act, stream=stream)
         ctx.sim = sim
+        ctx.stream = stream
         ctx.save_for_backward(q_traj, qd_traj, act)
         return q_traj, qd_traj, rew
 
@@ -215,8 +222,9 @@ class SimWindow(torch.autograd.Function):
         sim = ctx.sim
         q_traj, qd_traj, act = ctx.saved_tensors
         h = act.shape[0]
-        gq = torch.zeros_like(q_traj) if gq is None else gq.contiguous()
-        gqd = torch.zeros_like(qd_traj) if gqd is None else gqd.contiguous()
-        gr = torch.zeros(h, sim.n_envs, device=sim.device) if gr is None else gr.contiguous()
-        q0b, qd0b, ab = sim.window_adjoint(q_traj, qd_traj, act, gr, gq, gqd)
+        with torch.cuda.stream(ctx.stream):
+            gq = torch.zeros_like(q_traj) if gq is None else gq.contiguous()
+            gqd = torch.zeros_like(qd_traj) if gqd is None else gqd.contiguous()
+            gr = torch.zeros(h, sim.n_envs, device=sim.device) if gr is None else gr.contiguous()
+            q0b, qd0b, ab = sim.window_adjoint(q_traj, qd_traj, act, gr, gq, gqd, stream=ctx.stream)
         return None, q0b, qd0b, ab

@@ -80,12 +80,12 @@ def test_policy_window_graph_capture_replays_forward_and_backward():
     N, h = 4, 3
     m, sim, pol, q0, qd0 = _setup(N, h, seed=1)
     params = list(pol.parameters())
-    loss_ref = policy_window_loss(sim, pol, q0, qd0, h)
-    g_ref = torch.autograd.grad(loss_ref, params)
     s = torch.cuda.Stream()
     s.wait_stream(torch.cuda.current_stream())
-    with torch.cuda.stream(s):
-        for _ in range(2):   # warm-up on the side stream
+    with torch.cuda.stream(s):   # eager reference and warm-up on a side stream, never the legacy one
+        loss_ref = policy_window_loss(sim, pol, q0, qd0, h)
+        g_ref = torch.autograd.grad(loss_ref, params)
+        for _ in range(2):
             torch.autograd.grad(policy_window_loss(sim, pol, q0, qd0, h), params)
     torch.cuda.current_stream().wait_stream(s)
     graph = torch.cuda.CUDAGraph()

@@ -81,7 +81,7 @@ static void compute_layout(shac_model* m) {
   take(d.o_QC, m->nq); take(d.o_QDC, nv); take(d.o_A, 6 * L); take(d.o_F, 6 * L); take(d.o_IC, 10 * L);
   take(d.o_B, nv); take(d.o_T, nv);
   take(d.o_LAM, nv); take(d.o_VB, 6 * L); take(d.o_AB, 6 * L); take(d.o_FB, 6 * L);
-  take(d.o_SIB, 12 * L); take(d.o_RB, 9 * L); take(d.o_PB, 3 * L); take(d.o_ITB, 10 * ni); take(d.o_TP, 12 * L);
+  take(d.o_RB, 9 * L); take(d.o_PB, 3 * L); take(d.o_ITB, 10 * ni); take(d.o_TP, 12 * L);
   take(d.o_SEGA, m->nseg);
   d.env_floats = o;
 }
@@ -306,13 +306,13 @@ static int default_lanes(const shac_model* m) {
   return 32;
 }
 
-// Register row capacity of the batched dense path: a team needs one lane per
-// DOF; 0 selects the shared-memory form.
+// Register row capacity of the batched dense path (2, 4, 8, 12, ..., 32: the
+// device instantiations): a team needs one lane per padded row; 0 selects the
+// shared-memory form.
 static int dense_class(int nv, int lanes) {
-  if (lanes < nv) return 0;
-  if (nv <= 8) return 8;
-  if (nv <= 16) return 16;
-  return 32;
+  if (lanes < 2 || lanes < nv || nv > 32) return 0;
+  const int nm = nv <= 2 ? 2 : nv <= 4 ? 4 : ((nv + 3) / 4) * 4;
+  return nm <= lanes ? nm : 0;
 }
 
 static int env_stride(const shac_model* m) { return ((m->layout.env_floats + 31) / 32) * 32 + 1; }
@@ -507,7 +507,9 @@ static shac_status batched_launch(shac_batch* b, BatchedArgs& a, void* ws, cudaS
   if (W < 1) return SHAC_ERR_CAPACITY;
   const size_t smem = (size_t)W * a.smem_warp_floats * sizeof(float);
   const int block = 32 * W;
-  if (smem > 48 * 1024 && batched_set_smem_limit(smem) != cudaSuccess) return SHAC_ERR_CAPACITY;
+  // Static plus dynamic shared memory above 48 KB needs the opt-in attribute;
+  // the kernels' static part (the model table) is under 8 KB.
+  if (smem > 40 * 1024 && batched_set_smem_limit(smem) != cudaSuccess) return SHAC_ERR_CAPACITY;
   int occ = 0;
   if (batched_occupancy(&occ, block, smem, adjoint) != cudaSuccess) return SHAC_ERR_CUDA;
   if (occ < 1) return SHAC_ERR_CAPACITY;

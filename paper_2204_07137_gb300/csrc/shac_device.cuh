@@ -32,6 +32,7 @@
 // that a team performs in a different order (there is none: every
 // reduction below is a fixed-order gather).
 #pragma once
+#include <utility>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -74,7 +75,7 @@ struct DevModel {
   int o_Q, o_QD, o_ACT, o_QB, o_QDB, o_ACTB;
   int o_R, o_P, o_SI, o_S, o_V, o_A, o_F, o_FX, o_IT, o_IC, o_M, o_LD, o_B, o_T, o_QDD;
   int o_QC, o_QDC;                       // compensation (low parts) of q, qd within a step
-  int o_LAM, o_VB, o_AB, o_FB, o_SIB, o_RB, o_PB, o_ITB, o_TP, o_SEGA;
+  int o_LAM, o_VB, o_AB, o_FB, o_RB, o_PB, o_ITB, o_TP, o_SEGA;
   int rec_floats;       // floats of the substep record: scratch [0, rec_floats) (o_Q first)
   int env_floats;
 };
@@ -263,19 +264,20 @@ __device__ __forceinline__ void lk_muscle_wrench(const DevModel& M, const Mem& w
 // sweeps) or child-first (leaves-first sweeps); one team barrier per chain level.
 __device__ __forceinline__ int chain_next(const DevModel& M, int i) { return __ldg(M.ch_idx + __ldg(M.ch_ptr + i)); }
 
-// All of sweep 1's work for link i in one pass, values kept in registers:
-// forward kinematics from the parent (rotation R_i, origin P_i), the spatial
-// inertia about the reference point (m, h = m c, Io), the motion-subspace
-// columns (revolute (a, P x a), prismatic (0, a), free (R e_k, P x R e_k) for
-// the body rates and (0, R e_k) for v_body), the velocity V_i = V_p + u_i, the
-// Newton-Euler acceleration A_i = A_p + V_i x u_i with qdd = 0 (gravity enters
-// as the base acceleration -g), the contact forces and the local force
-// F_i = I_i A_i + V_i x* (I_i V_i) - Fext_i.
+// Sweep 1 is split in two passes.  The root-first pass carries what flows
+// down the tree (lk_kin); everything else a link needs is local to it and
+// runs with one lane per link for all links at once (lk_local), so the
+// sequential critical path holds only the light kinematic recursion.
+//
+// lk_kin: forward kinematics from the parent (rotation R_i, origin P_i), the
+// motion-subspace columns (revolute (a, P x a), prismatic (0, a), free
+// (R e_k, P x R e_k) for the body rates and (0, R e_k) for v_body), the
+// velocity V_i = V_p + u_i and the Newton-Euler acceleration
+// A_i = A_p + V_i x u_i with qdd = 0 (gravity enters as the base acceleration -g).
 template <class Mem>
-__device__ __forceinline__ void lk_forward(const DevModel& M, const Mem& w, int i) {
+__device__ __forceinline__ void lk_kin(const DevModel& M, const Mem& w, int i) {
   const int jt = __ldg(M.jtype + i), s = __ldg(M.qs + i), p = __ldg(M.parent + i);
   const int d0 = __ldg(M.ds + i), nd = __ldg(M.nd + i);
-  // kinematics
   M33 R;
   V3 P;
   const V3 ax = cld3(M.axis + 3 * i);
@@ -285,18 +287,58 @@ __device__ __forceinline__ void lk_forward(const DevModel& M, const Mem& w, int 
   } else {
     M33 Rj = cldm(M.jrot + 9 * i);
     V3 Pj = cld3(M.jpos + 3 * i);
+    if (jt == J_REV) Rj = mul(Rj, axis_angle(ax, w[M.o_Q + s]));   // independent of the parent
     if (p >= 0) {
       const M33 Rp = ldm(w, M.o_R + 9 * p);
       Pj = ld3(w, M.o_P + 3 * p) + mul(Rp, Pj);
       Rj = mul(Rp, Rj);
     }
-    if (jt == J_REV) { R = mul(Rj, axis_angle(ax, w[M.o_Q + s])); P = Pj; }
-    else if (jt == J_PRIS) { R = Rj; P = Pj + w[M.o_Q + s] * mul(Rj, ax); }
-    else { R = Rj; P = Pj; }
+    R = Rj;
+    P = Pj;
+    if (jt == J_PRIS) P = Pj + w[M.o_Q + s] * mul(Rj, ax);
   }
   stm(w, M.o_R + 9 * i, R);
   st3(w, M.o_P + 3 * i, P);
-  // spatial inertia about the reference point
+  V3 uw = v3(0.f, 0.f, 0.f), uv = v3(0.f, 0.f, 0.f);
+  for (int k = 0; k < nd; ++k) {
+    V3 sw, sv;
+    if (jt == J_FREE) {
+      if (k < 3) { sw = col(R, k); sv = cross(P, sw); }
+      else { sw = v3(0.f, 0.f, 0.f); sv = col(R, k - 3); }
+    } else {
+      const V3 a = mul(R, ax);
+      if (jt == J_REV) { sw = a; sv = cross(P, a); }
+      else { sw = v3(0.f, 0.f, 0.f); sv = a; }
+    }
+    st3(w, M.o_S + 6 * (d0 + k), sw);
+    st3(w, M.o_S + 6 * (d0 + k) + 3, sv);
+    const float qd = w[M.o_QD + d0 + k];
+    uw = uw + qd * sw;
+    uv = uv + qd * sv;
+  }
+  V3 Vw = uw, Vv = uv, aw, av;
+  if (p >= 0) {
+    Vw = Vw + ld3(w, M.o_V + 6 * p); Vv = Vv + ld3(w, M.o_V + 6 * p + 3);
+    aw = ld3(w, M.o_A + 6 * p); av = ld3(w, M.o_A + 6 * p + 3);
+  } else {
+    aw = v3(0.f, 0.f, 0.f); av = v3(-M.grav[0], -M.grav[1], -M.grav[2]);
+  }
+  aw = aw + cross(Vw, uw);
+  av = av + cross(Vw, uv) + cross(Vv, uw);
+  st3(w, M.o_V + 6 * i, Vw); st3(w, M.o_V + 6 * i + 3, Vv);
+  st3(w, M.o_A + 6 * i, aw); st3(w, M.o_A + 6 * i + 3, av);
+}
+
+// lk_local: the spatial inertia about the reference point (m, h = m c, Io),
+// the contact forces of link i and its local force
+// F_i = I_i A_i + V_i x* (I_i V_i) - Fext_i, from the pose, velocity and
+// acceleration lk_kin stored.
+template <class Mem>
+__device__ __forceinline__ void lk_local(const DevModel& M, const Mem& w, int i) {
+  const M33 R = ldm(w, M.o_R + 9 * i);
+  const V3 P = ld3(w, M.o_P + 3 * i);
+  const V3 Vw = ld3(w, M.o_V + 6 * i), Vv = ld3(w, M.o_V + 6 * i + 3);
+  const V3 aw = ld3(w, M.o_A + 6 * i), av = ld3(w, M.o_A + 6 * i + 3);
   const float m = __ldg(M.mass + i);
   const V3 c = P + mul(R, cld3(M.com + 3 * i));
   const M33 Iw = mulBT(mul(R, com_inertia(M, i)), R);
@@ -315,36 +357,6 @@ __device__ __forceinline__ void lk_forward(const DevModel& M, const Mem& w, int 
             ixz * xw.x + iyz * xw.y + izz * xw.z) + cross(h, xv);
     yf = m * xv - cross(h, xw);
   };
-  // motion subspaces and joint velocity u = sum S qd
-  V3 uw = v3(0.f, 0.f, 0.f), uv = v3(0.f, 0.f, 0.f);
-  for (int k = 0; k < nd; ++k) {
-    V3 sw, sv;
-    if (jt == J_FREE) {
-      if (k < 3) { sw = col(R, k); sv = cross(P, sw); }
-      else { sw = v3(0.f, 0.f, 0.f); sv = col(R, k - 3); }
-    } else {
-      const V3 a = mul(R, ax);
-      if (jt == J_REV) { sw = a; sv = cross(P, a); }
-      else { sw = v3(0.f, 0.f, 0.f); sv = a; }
-    }
-    st3(w, M.o_S + 6 * (d0 + k), sw);
-    st3(w, M.o_S + 6 * (d0 + k) + 3, sv);
-    const float qd = w[M.o_QD + d0 + k];
-    uw = uw + qd * sw;
-    uv = uv + qd * sv;
-  }
-  // velocity and acceleration (qdd = 0; gravity as base acceleration)
-  V3 Vw = uw, Vv = uv, aw, av;
-  if (p >= 0) {
-    Vw = Vw + ld3(w, M.o_V + 6 * p); Vv = Vv + ld3(w, M.o_V + 6 * p + 3);
-    aw = ld3(w, M.o_A + 6 * p); av = ld3(w, M.o_A + 6 * p + 3);
-  } else {
-    aw = v3(0.f, 0.f, 0.f); av = v3(-M.grav[0], -M.grav[1], -M.grav[2]);
-  }
-  aw = aw + cross(Vw, uw);
-  av = av + cross(Vw, uv) + cross(Vv, uw);
-  st3(w, M.o_V + 6 * i, Vw); st3(w, M.o_V + 6 * i + 3, Vv);
-  st3(w, M.o_A + 6 * i, aw); st3(w, M.o_A + 6 * i + 3, av);
   // Sec. 3.1 contact model on the ground plane z = 0 (n = +z) for the contact
   // spheres of link i, applied at the lowest point x of each sphere:
   //   f_n = (-ke + kd ddot) min(d, 0),  d = height of x, ddot = v_x . n
@@ -378,7 +390,6 @@ __device__ __forceinline__ void lk_forward(const DevModel& M, const Mem& w, int 
   }
   st3(w, M.o_FX + 6 * i, wn);
   st3(w, M.o_FX + 6 * i + 3, wf);
-  // local force F = I A + V x* (I V) - Fext
   V3 fn, ff, bn, bf;
   imul(aw, av, fn, ff);
   imul(Vw, Vv, bn, bf);
@@ -388,21 +399,24 @@ __device__ __forceinline__ void lk_forward(const DevModel& M, const Mem& w, int 
   st3(w, M.o_F + 6 * i + 3, ff);
 }
 
-// Sweep 1, root first: kinematics, inertias, subspaces, velocities, contact
-// forces, Newton-Euler accelerations (qdd = 0) and local forces of every link;
-// then the muscle wrenches (their segments span two links).
+// Sweep 1: root first the kinematics, subspaces, velocities and Newton-Euler
+// accelerations (qdd = 0) of every link; then, one lane per link, the
+// inertias, contact forces and local forces; then the muscle wrenches (their
+// segments span two links).
 template <class Mem>
 __device__ void sw_forward(const DevModel& M, const Mem& w, int lane, int nl) {
   for (int l = 0; l < M.nlev; ++l) {
     for (int ii = __ldg(M.lvl_ptr + l) + lane; ii < __ldg(M.lvl_ptr + l + 1); ii += nl) {
       const int hd = __ldg(M.lvl_link + ii), tl = __ldg(M.chain_tail + hd);
       for (int i = hd;; i = chain_next(M, i)) {
-        lk_forward(M, w, i);
+        lk_kin(M, w, i);
         if (i == tl) break;
       }
     }
     team_sync(nl);
   }
+  for (int i = lane; i < M.L; i += nl) lk_local(M, w, i);
+  team_sync(nl);
   if (M.nseg > 0) {
     for (int sg = lane; sg < M.nseg; sg += nl) seg_forward(M, w, sg);
     team_sync(nl);
@@ -613,100 +627,188 @@ __device__ __forceinline__ void clear_comp(const DevModel& M, const Mem& w, int 
 
 // ---- register-resident dense path (teams with at least nv lanes) ----------
 // Lane a of the team owns row a of M and DOF a of the right-hand side.  The
-// row is assembled in registers (CRBA part 2, ancestor DOFs from a bit mask),
-// factorised by a right-looking Cholesky whose column k is broadcast with team
-// shuffles, and the factor is stored to o_M/o_LD for the backward pass.  NM >=
-// nv is the register capacity of a row (compile-time), nl >= nv the team size.
-template <int NM, class Mem>
-__device__ void dense_factor(const DevModel& M, const Mem& w, int lane, int nl) {
-  const int n = M.nv;
-  const bool own = lane < n;
-  float row[NM];
-  {
-    V3 fn = v3(0.f, 0.f, 0.f), ff = v3(0.f, 0.f, 0.f);
-    unsigned mask = 0u;
-    if (own) {
-      const int i = __ldg(M.dof_link + lane);
-      si_mul(w, M.o_IC + 10 * i, ld3(w, M.o_S + 6 * lane), ld3(w, M.o_S + 6 * lane + 3), fn, ff);
-      mask = __ldg(M.anc_mask + lane);
-    }
-    const float arm = own ? __ldg(M.arm + lane) : 1.f;
-#pragma unroll
-    for (int b = 0; b < NM; ++b) {
-      float v = 0.f;
-      if ((mask >> b) & 1u) v = dot(ld3(w, M.o_S + 6 * b), fn) + dot(ld3(w, M.o_S + 6 * b + 3), ff);
-      if (b == lane) v += arm;
-      row[b] = v;
-    }
-  }
-#pragma unroll
-  for (int k = 0; k < NM; ++k) {
-    if (k < n) {
-      const float rk = row[k];
-      const float dkk = sqrtf(__shfl_sync(0xffffffffu, rk, k, nl));
-      const float lik = rk * (1.f / dkk);
-      if (lane > k) row[k] = lik;
-      else if (lane == k) row[k] = dkk;
-#pragma unroll
-      for (int j = k + 1; j < NM; ++j) {
-        if (j < n) {
-          const float ljk = __shfl_sync(0xffffffffu, lik, j, nl);
-          if (lane >= j) row[j] -= lik * ljk;
-        }
-      }
-    }
-  }
-  if (own) {
-#pragma unroll
-    for (int b = 0; b < NM; ++b) {
-      if (b < lane) w[M.o_M + lane * n + b] = row[b];
-      else if (b == lane) w[M.o_LD + lane] = row[b];
-    }
-  }
-  team_sync(nl);
+// matrix is padded to NM x NM (nv <= NM <= team size) with identity rows.
+// Every column loop is expanded at compile time through index sequences, so
+// each row element is a named register (a runtime-bounded or partially
+// unrolled loop would leave the row array in local memory) and no shuffle
+// sits under a lane-dependent branch.  The row is assembled in registers
+// (CRBA part 2, ancestor DOFs from a bit mask) and factorised by a
+// right-looking Cholesky whose column k is broadcast with team shuffles; the
+// strict lower part of L goes to o_M and the reciprocal diagonal 1/L_kk to
+// o_LD for the solves and the backward pass.
+
+// row[J] -= L_ik L_jk for the lanes i >= J of the trailing block.
+template <int J, int NM>
+__device__ __forceinline__ void chol_update(float (&row)[NM], float lik, int lane, int nl) {
+  const float ljk = __shfl_sync(0xffffffffu, lik, J, nl);   // every lane takes part
+  if (lane >= J) row[J] = fmaf(-lik, ljk, row[J]);
+}
+template <int K, int NM, int... J>
+__device__ __forceinline__ void chol_trailing(float (&row)[NM], float lik, int lane, int nl,
+                                              std::integer_sequence<int, J...>) {
+  (chol_update<K + 1 + J, NM>(row, lik, lane, nl), ...);
+}
+// Column K: L_KK = sqrt(pivot) (lane K), L_iK = M_iK / L_KK (lanes i > K).
+template <int K, int NM>
+__device__ __forceinline__ void chol_column(float (&row)[NM], float& inv_diag, int lane, int nl) {
+  const float rk = row[K];
+  const float inv = rsqrtf(__shfl_sync(0xffffffffu, rk, K, nl));
+  const float lik = rk * inv;
+  if (lane >= K) row[K] = lik;
+  if (lane == K) inv_diag = inv;
+  chol_trailing<K, NM>(row, lik, lane, nl, std::make_integer_sequence<int, NM - K - 1>{});
+}
+template <int NM, int... K>
+__device__ __forceinline__ void chol_columns(float (&row)[NM], float& inv_diag, int lane, int nl,
+                                             std::integer_sequence<int, K...>) {
+  (chol_column<K, NM>(row, inv_diag, lane, nl), ...);
 }
 
-// x = (L L^T)^{-1} b with the stored factor; lane a holds b_a (register),
-// the substitution columns are broadcast with team shuffles (no barriers).
-template <class Mem>
-__device__ __forceinline__ float dense_solve_reg(const DevModel& M, const Mem& w, int lane, int nl, float b) {
+// Forward substitution y = L^{-1} b, step K: lane a holds b_a, row a of L in
+// its registers.
+template <int K, int NM>
+__device__ __forceinline__ void fsub_step(const float (&row)[NM], float inv_diag, float& b, int lane, int nl) {
+  const float yk = __shfl_sync(0xffffffffu, b * inv_diag, K, nl);
+  if (lane > K) b = fmaf(-row[K], yk, b);
+  else if (lane == K) b = yk;
+}
+template <int NM, int... K>
+__device__ __forceinline__ void fsub(const float (&row)[NM], float inv_diag, float& b, int lane, int nl,
+                                     std::integer_sequence<int, K...>) {
+  (fsub_step<K, NM>(row, inv_diag, b, lane, nl), ...);
+}
+// Backward substitution x = L^{-T} y, step K (descending): lane a < K needs
+// L_Ka, read from the stored factor; the address is always valid so the load
+// does not wait on the substitution chain.
+template <int K, class Mem>
+__device__ __forceinline__ void bsub_step(const DevModel& M, const Mem& w, float inv_diag, float& b, int lane,
+                                          int nl) {
   const int n = M.nv;
-  const bool own = lane < n;
-  const float invd = own ? 1.f / w[M.o_LD + lane] : 0.f;
-  for (int k = 0; k < n; ++k) {
-    const float yk = __shfl_sync(0xffffffffu, b * invd, k, nl);
-    if (lane > k && own) b -= w[M.o_M + lane * n + k] * yk;
-    else if (lane == k) b = yk;
-  }
-  for (int k = n - 1; k >= 0; --k) {
-    const float xk = __shfl_sync(0xffffffffu, b * invd, k, nl);
-    if (lane < k) b -= w[M.o_M + k * n + lane] * xk;
-    else if (lane == k) b = xk;
-  }
-  return b;
+  const bool use = lane < K && K < n;
+  const float lka = w[M.o_M + (use ? K * n + lane : 0)];
+  const float xk = __shfl_sync(0xffffffffu, b * inv_diag, K, nl);
+  if (use) b = fmaf(-lka, xk, b);
+  else if (lane == K) b = xk;
+}
+template <int NM, class Mem, int... K>
+__device__ __forceinline__ void bsub(const DevModel& M, const Mem& w, float inv_diag, float& b, int lane, int nl,
+                                     std::integer_sequence<int, K...>) {
+  (bsub_step<NM - 1 - K>(M, w, inv_diag, b, lane, nl), ...);
 }
 
-template <class Mem>
-__device__ void dense_solve(const DevModel& M, const Mem& w, int lane, int nl, int o_in, int o_out) {
+// Row a of M (CRBA part 2) into registers; padding rows are identity rows.
+template <int B, int NM, class Mem>
+__device__ __forceinline__ void row_entry(const DevModel& M, const Mem& w, float (&row)[NM], unsigned mask, V3 fn,
+                                          V3 ff, float arm, int lane) {
+  float v = 0.f;
+  if ((mask >> B) & 1u) v = dot(ld3(w, M.o_S + 6 * B), fn) + dot(ld3(w, M.o_S + 6 * B + 3), ff);
+  if (B == lane) v += arm;
+  row[B] = v;
+}
+template <int NM, class Mem, int... B>
+__device__ __forceinline__ void row_assemble(const DevModel& M, const Mem& w, float (&row)[NM], int lane,
+                                             std::integer_sequence<int, B...>) {
+  V3 fn = v3(0.f, 0.f, 0.f), ff = v3(0.f, 0.f, 0.f);
+  unsigned mask = 0u;
   const bool own = lane < M.nv;
-  const float x = dense_solve_reg(M, w, lane, nl, own ? w[o_in + lane] : 0.f);
-  if (own) w[o_out + lane] = x;
+  if (own) {
+    const int i = __ldg(M.dof_link + lane);
+    si_mul(w, M.o_IC + 10 * i, ld3(w, M.o_S + 6 * lane), ld3(w, M.o_S + 6 * lane + 3), fn, ff);
+    mask = __ldg(M.anc_mask + lane);
+  }
+  const float arm = own ? __ldg(M.arm + lane) : 1.f;
+  (row_entry<B, NM>(M, w, row, mask, fn, ff, arm, lane), ...);
+}
+template <int B, int NM, class Mem>
+__device__ __forceinline__ void row_store_entry(const DevModel& M, const Mem& w, const float (&row)[NM], int lane) {
+  if (B < lane && lane < M.nv) w[M.o_M + lane * M.nv + B] = row[B];
+}
+template <int NM, class Mem, int... B>
+__device__ __forceinline__ void row_store(const DevModel& M, const Mem& w, const float (&row)[NM], int lane,
+                                          std::integer_sequence<int, B...>) {
+  (row_store_entry<B, NM>(M, w, row, lane), ...);
+}
+template <int B, int NM, class Mem>
+__device__ __forceinline__ void row_load_entry(const DevModel& M, const Mem& w, float (&row)[NM], int lane) {
+  const bool use = B < lane && lane < M.nv;
+  const float v = w[M.o_M + (use ? lane * M.nv + B : 0)];
+  row[B] = use ? v : 0.f;
+}
+template <int NM, class Mem, int... B>
+__device__ __forceinline__ void row_load(const DevModel& M, const Mem& w, float (&row)[NM], int lane,
+                                         std::integer_sequence<int, B...>) {
+  (row_load_entry<B, NM>(M, w, row, lane), ...);
+}
+
+// Forward substep's dense part: assemble, factor, store the factor, solve
+// (M + diag(arm)) qdd = b into o_QDD.  b is lane a's right-hand side.
+template <int NM, class Mem>
+__device__ __forceinline__ void dense_substep(const DevModel& M, const Mem& w, int lane, int nl, float b) {
+  using Seq = std::make_integer_sequence<int, NM>;
+  const bool own = lane < M.nv;
+  float row[NM];
+  row_assemble<NM>(M, w, row, lane, Seq{});
+  float inv_diag = 1.f;
+  chol_columns<NM>(row, inv_diag, lane, nl, Seq{});
+  row_store<NM>(M, w, row, lane, Seq{});
+  if (own) w[M.o_LD + lane] = inv_diag;
   team_sync(nl);
+  if (!own) b = 0.f;
+  fsub<NM>(row, inv_diag, b, lane, nl, Seq{});
+  bsub<NM>(M, w, inv_diag, b, lane, nl, Seq{});
+  if (own) w[M.o_QDD + lane] = b;
+  team_sync(nl);
+}
+
+// x = (L L^T)^{-1} b with the stored factor (o_M strict lower, o_LD = 1/L_kk):
+// o_in -> o_out.
+template <int NM, class Mem>
+__device__ __forceinline__ void dense_stored_solve(const DevModel& M, const Mem& w, int lane, int nl, int o_in,
+                                                   int o_out) {
+  using Seq = std::make_integer_sequence<int, NM>;
+  const bool own = lane < M.nv;
+  float row[NM];
+  row_load<NM>(M, w, row, lane, Seq{});
+  const float inv_diag = own ? w[M.o_LD + lane] : 1.f;
+  float b = own ? w[o_in + lane] : 0.f;
+  fsub<NM>(row, inv_diag, b, lane, nl, Seq{});
+  bsub<NM>(M, w, inv_diag, b, lane, nl, Seq{});
+  if (own) w[o_out + lane] = b;
+  team_sync(nl);
+}
+
+// Row capacities of the register path (see dense_class on the host).
+#define SHAC_DENSE_CASES(X) X(2) X(4) X(8) X(12) X(16) X(20) X(24) X(28) X(32)
+
+template <class Mem>
+__device__ __forceinline__ void dense_substep_nm(const DevModel& M, const Mem& w, int lane, int nl, int nm, float b) {
+  switch (nm) {
+#define SHAC_CASE(N) case N: dense_substep<N>(M, w, lane, nl, b); break;
+    SHAC_DENSE_CASES(SHAC_CASE)
+#undef SHAC_CASE
+    default: break;
+  }
+}
+template <class Mem>
+__device__ __forceinline__ void dense_stored_solve_nm(const DevModel& M, const Mem& w, int lane, int nl, int nm,
+                                                      int o_in, int o_out) {
+  switch (nm) {
+#define SHAC_CASE(N) case N: dense_stored_solve<N>(M, w, lane, nl, o_in, o_out); break;
+    SHAC_DENSE_CASES(SHAC_CASE)
+#undef SHAC_CASE
+    default: break;
+  }
 }
 
 // One forward substep up to the accelerations (integration is separate).
-// NM = 0: shared-memory dense stages (any team size, incl. one thread per
-// environment); NM > 0: register-resident dense path.
-template <int NM, class Mem>
-__device__ void substep_dynamics(const DevModel& M, const Mem& w, int lane, int nl) {
+// nm = 0: shared-memory dense stages (any team size, incl. one thread per
+// environment); nm > 0: register-resident dense path of that row capacity.
+template <class Mem>
+__device__ void substep_dynamics(const DevModel& M, const Mem& w, int lane, int nl, int nm) {
   sw_forward(M, w, lane, nl);
   sw_gather(M, w, lane, nl, true);
-  if constexpr (NM > 0) {
-    const float b = lane < M.nv ? dof_rhs(M, w, lane) : 0.f;
-    dense_factor<NM>(M, w, lane, nl);
-    const float x = dense_solve_reg(M, w, lane, nl, b);
-    if (lane < M.nv) w[M.o_QDD + lane] = x;
-    team_sync(nl);
+  if (nm > 0) {
+    dense_substep_nm(M, w, lane, nl, nm, lane < M.nv ? dof_rhs(M, w, lane) : 0.f);
   } else {
     st_rhs(M, w, lane, nl);
     st_mass_rows(M, w, lane, nl);
@@ -762,16 +864,6 @@ __device__ void reward_adjoint(const DevModel& M, const Mem& w, float rb) {
       w[M.o_QB + 2] += dD * rb;
     }
   }
-}
-
-// y_bar, x -> accumulate cotangents of the 10-float spatial inertia for y = I x
-// into (hbar[3], G[9]) at o (mass cotangent not needed: masses are constants).
-template <class Mem>
-__device__ __forceinline__ void si_mul_adj(const Mem& w, int o, V3 xw, V3 xv, V3 yn_b, V3 yf_b) {
-  add3(w, o, cross(xv, yn_b) + cross(yf_b, xw));
-  w[o + 3] += yn_b.x * xw.x; w[o + 4] += yn_b.x * xw.y; w[o + 5] += yn_b.x * xw.z;
-  w[o + 6] += yn_b.y * xw.x; w[o + 7] += yn_b.y * xw.y; w[o + 8] += yn_b.y * xw.z;
-  w[o + 9] += yn_b.z * xw.x; w[o + 10] += yn_b.z * xw.y; w[o + 11] += yn_b.z * xw.z;
 }
 
 // Zero a range of scratch (team-parallel).
@@ -842,38 +934,16 @@ __device__ __forceinline__ void add_outer(M33& A, V3 a, V3 b) {   // A += a b^T
   A.m[6] += a.z * b.x; A.m[7] += a.z * b.y; A.m[8] += a.z * b.z;
 }
 
-// Adjoint sweep 1 (root first) at link i, with w = -lambda as the cotangent
-// of tau = S^T F_total (G = ID(q, qd, qdd) + arm qdd - tau_j):
-//  * accelerations A_i and local force F_i recomputed with the solved qdd;
-//  * F_bar_i = sum_{d in i} w_d S_d + F_bar_parent;
-//  * reverse of F_i = I A + V x* (I V) - Fext: A_bar (local), I_bar, V_bar;
-//  * joint forces (actuation, limits, damping) of the DOFs of i;
-//  * the contacts of link i (their external wrench enters F_i with a minus).
+// Adjoint sweep 1 is split like the forward sweep, with w = -lambda as the
+// cotangent of tau = S^T F_total (G = ID(q, qd, qdd) + arm qdd - tau_j).
+//
+// lk_adj_acc, root first: the accelerations A_i = A_p + sum_{d in i} S_d qdd_d
+// + V_i x u_i with the solved qdd, and the force cotangent
+// F_bar_i = F_bar_p + sum_{d in i} w_d S_d.
 template <class Mem>
-__device__ __forceinline__ void lk_adj_fwd(const DevModel& M, const Mem& w, int i) {
-  // own accumulators
-#pragma unroll
-  for (int k = 0; k < 6; ++k) w[M.o_VB + 6 * i + k] = 0.f;
-#pragma unroll
-  for (int k = 0; k < 12; ++k) w[M.o_SIB + 12 * i + k] = 0.f;
-#pragma unroll
-  for (int k = 0; k < 9; ++k) w[M.o_RB + 9 * i + k] = 0.f;
-  w[M.o_PB + 3 * i] = 0.f; w[M.o_PB + 3 * i + 1] = 0.f; w[M.o_PB + 3 * i + 2] = 0.f;
-  const int p = __ldg(M.parent + i), d0 = __ldg(M.ds + i), nd = __ldg(M.nd + i), jt = __ldg(M.jtype + i);
-  const int osi = M.o_SI + 10 * i, osb = M.o_SIB + 12 * i;
-  // spatial inertia in registers
-  const float m = w[osi];
-  const V3 h = ld3(w, osi + 1);
-  const float ixx = w[osi + 4], iyy = w[osi + 5], izz = w[osi + 6], ixy = w[osi + 7], ixz = w[osi + 8],
-              iyz = w[osi + 9];
-  auto imul = [&](V3 xw, V3 xv, V3& yn, V3& yf) {
-    yn = v3(ixx * xw.x + ixy * xw.y + ixz * xw.z, ixy * xw.x + iyy * xw.y + iyz * xw.z,
-            ixz * xw.x + iyz * xw.y + izz * xw.z) + cross(h, xv);
-    yf = m * xv - cross(h, xw);
-  };
+__device__ __forceinline__ void lk_adj_acc(const DevModel& M, const Mem& w, int i) {
+  const int p = __ldg(M.parent + i), d0 = __ldg(M.ds + i), nd = __ldg(M.nd + i);
   const V3 Vw = ld3(w, M.o_V + 6 * i), Vv = ld3(w, M.o_V + 6 * i + 3);
-  // accelerations with the solved qdd, local force F = I A + V x* (I V) - Fext,
-  // and the force cotangent F_bar = sum_{d in i} (-lambda_d) S_d + F_bar_parent
   V3 aw, av, nb = v3(0.f, 0.f, 0.f), fb = v3(0.f, 0.f, 0.f);
   if (p >= 0) {
     aw = ld3(w, M.o_A + 6 * p); av = ld3(w, M.o_A + 6 * p + 3);
@@ -888,7 +958,34 @@ __device__ __forceinline__ void lk_adj_fwd(const DevModel& M, const Mem& w, int 
     uw = uw + qd * sw; uv = uv + qd * sv;
     aw = aw + qdd * sw; av = av + qdd * sv;
     nb = nb - lam * sw; fb = fb - lam * sv;
-    // joint forces: tau_j_bar = lambda
+  }
+  aw = aw + cross(Vw, uw);
+  av = av + cross(Vw, uv) + cross(Vv, uw);
+  st3(w, M.o_A + 6 * i, aw); st3(w, M.o_A + 6 * i + 3, av);
+  st3(w, M.o_FB + 6 * i, nb); st3(w, M.o_FB + 6 * i + 3, fb);
+}
+
+// Cotangent of the spatial inertia from y = I x (y_bar given): h_bar and the
+// (full 3 x 3) cotangent G of Io, accumulated in registers (no mass
+// cotangent: masses are constants).
+__device__ __forceinline__ void si_adj(V3& hb, M33& G, V3 xw, V3 xv, V3 yn_b, V3 yf_b) {
+  hb = hb + cross(xv, yn_b) + cross(yf_b, xw);
+  add_outer(G, yn_b, xw);
+}
+
+// lk_adj_local, one lane per link, everything of adjoint sweep 1 that is local
+// to link i: the joint forces of its DOFs (actuation, limits, damping:
+// tau_j_bar = lambda); the local force F_i = I A + V x* (I V) - Fext
+// recomputed with the solved accelerations; the reverse of F_i (A_bar =
+// I F_bar, V_bar and the inertia cotangent, carried through h = m c,
+// Io = R Ic R^T + m(|c|^2 1 - c c^T), c = P + R com to the pose); and the
+// reverse of link i's contacts (their external wrench enters F_i with a
+// minus).  Stores link i's V_bar, R_bar and P_bar accumulators.
+template <class Mem>
+__device__ __forceinline__ void lk_adj_local(const DevModel& M, const Mem& w, int i) {
+  const int d0 = __ldg(M.ds + i), nd = __ldg(M.nd + i), jt = __ldg(M.jtype + i);
+  for (int d = d0; d < d0 + nd; ++d) {
+    const float lam = w[M.o_LAM + d];
     const int a = __ldg(M.dof_act + d);
     if (a >= 0) w[M.o_ACTB + a] += lam * __ldg(M.gear + d);
     if (jt == J_REV || jt == J_PRIS) {
@@ -898,9 +995,19 @@ __device__ __forceinline__ void lk_adj_fwd(const DevModel& M, const Mem& w, int 
     }
     w[M.o_QDB + d] -= lam * __ldg(M.damp + d);
   }
-  aw = aw + cross(Vw, uw);
-  av = av + cross(Vw, uv) + cross(Vv, uw);
-  st3(w, M.o_A + 6 * i, aw); st3(w, M.o_A + 6 * i + 3, av);
+  const int osi = M.o_SI + 10 * i;
+  const float m = w[osi];
+  const V3 h = ld3(w, osi + 1);
+  const float ixx = w[osi + 4], iyy = w[osi + 5], izz = w[osi + 6], ixy = w[osi + 7], ixz = w[osi + 8],
+              iyz = w[osi + 9];
+  auto imul = [&](V3 xw, V3 xv, V3& yn, V3& yf) {
+    yn = v3(ixx * xw.x + ixy * xw.y + ixz * xw.z, ixy * xw.x + iyy * xw.y + iyz * xw.z,
+            ixz * xw.x + iyz * xw.y + izz * xw.z) + cross(h, xv);
+    yf = m * xv - cross(h, xw);
+  };
+  const V3 Vw = ld3(w, M.o_V + 6 * i), Vv = ld3(w, M.o_V + 6 * i + 3);
+  const V3 aw = ld3(w, M.o_A + 6 * i), av = ld3(w, M.o_A + 6 * i + 3);
+  const V3 nb = ld3(w, M.o_FB + 6 * i), fb = ld3(w, M.o_FB + 6 * i + 3);
   {
     V3 fn, ff, bn, bf;
     imul(aw, av, fn, ff);
@@ -909,14 +1016,16 @@ __device__ __forceinline__ void lk_adj_fwd(const DevModel& M, const Mem& w, int 
     ff = ff + cross(Vw, bf) - ld3(w, M.o_FX + 6 * i + 3);
     st3(w, M.o_F + 6 * i, fn); st3(w, M.o_F + 6 * i + 3, ff);
   }
-  st3(w, M.o_FB + 6 * i, nb);
-  st3(w, M.o_FB + 6 * i + 3, fb);
   // A_bar = I F_bar (I symmetric)
   V3 abn, abf;
   imul(nb, fb, abn, abf);
   st3(w, M.o_AB + 6 * i, abn);
   st3(w, M.o_AB + 6 * i + 3, abf);
-  si_mul_adj(w, osb, aw, av, nb, fb);
+  V3 hb = v3(0.f, 0.f, 0.f);
+  M33 G;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) G.m[k] = 0.f;
+  si_adj(hb, G, aw, av, nb, fb);
   // momentum B = I V and V x* B
   V3 Bn, Bf;
   imul(Vw, Vv, Bn, Bf);
@@ -928,13 +1037,30 @@ __device__ __forceinline__ void lk_adj_fwd(const DevModel& M, const Mem& w, int 
   imul(Bnb, Bfb, t1, t2);
   vwb = vwb + t1;
   vvb = vvb + t2;
-  si_mul_adj(w, osb, Vw, Vv, Bnb, Bfb);
-  // contacts of link i: Fext cotangent = -F_bar
-  const int k0 = __ldg(M.li_ptr + i), k1 = __ldg(M.li_ptr + i + 1);
+  si_adj(hb, G, Vw, Vv, Bnb, Bfb);
+  // spatial inertia about the reference point -> pose cotangents
+  const M33 R = ldm(w, M.o_R + 9 * i);
+  const V3 P = ld3(w, M.o_P + 3 * i);
   V3 Pb = v3(0.f, 0.f, 0.f);
   M33 Rb;
 #pragma unroll
   for (int k = 0; k < 9; ++k) Rb.m[k] = 0.f;
+  if (m != 0.f || __ldg(M.icom + 6 * i) != 0.f || __ldg(M.icom + 6 * i + 1) != 0.f || __ldg(M.icom + 6 * i + 2) != 0.f) {
+    const V3 com = cld3(M.com + 3 * i);
+    const V3 c = P + mul(R, com);
+    const float trG = G.m[0] + G.m[4] + G.m[8];
+    M33 Gs;   // G + G^T
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) Gs.m[3 * a + b] = G.m[3 * a + b] + G.m[3 * b + a];
+    const V3 cb = m * hb + m * (2.f * trG * c - mul(Gs, c));
+    Rb = mul(mul(Gs, R), com_inertia(M, i));
+    Pb = cb;
+    add_outer(Rb, cb, com);
+  }
+  // contacts of link i: Fext cotangent = -F_bar
+  const int k0 = __ldg(M.li_ptr + i), k1 = __ldg(M.li_ptr + i + 1);
   for (int k = k0; k < k1; ++k) {
     const int c = __ldg(M.li_idx + k);
     if (c >= M.nc) continue;
@@ -976,11 +1102,10 @@ __device__ __forceinline__ void lk_adj_fwd(const DevModel& M, const Mem& w, int 
     }
     w[M.o_ITB + 10 * c + 9] = db;
   }
-  add3(w, M.o_VB + 6 * i, vwb);
-  add3(w, M.o_VB + 6 * i + 3, vvb);
-  add3(w, M.o_PB + 3 * i, Pb);
-#pragma unroll
-  for (int k = 0; k < 9; ++k) w[M.o_RB + 9 * i + k] += Rb.m[k];
+  st3(w, M.o_VB + 6 * i, vwb);
+  st3(w, M.o_VB + 6 * i + 3, vvb);
+  st3(w, M.o_PB + 3 * i, Pb);
+  stm(w, M.o_RB + 9 * i, Rb);
 }
 
 // Reverse of one muscle segment: cotangents of both via points and of the
@@ -1016,8 +1141,9 @@ __device__ __forceinline__ void seg_adjoint(const DevModel& M, const Mem& w, int
 
 // Adjoint sweep 2 (leaves first) at link i: gather the children (total
 // forces, A_bar, V_bar, kinematic cotangents), reverse the Newton-Euler
-// accelerations and velocities, the motion subspaces and spatial inertia,
-// and the joint transform (forward kinematics).
+// accelerations and velocities, the motion subspaces and the joint transform
+// (forward kinematics).  The inertia's share of the pose cotangents was added
+// by lk_adj_local.
 template <class Mem>
 __device__ __forceinline__ void lk_adj_bwd(const DevModel& M, const Mem& w, int i) {
   const int c0 = __ldg(M.ch_ptr + i), c1 = __ldg(M.ch_ptr + i + 1);
@@ -1086,29 +1212,6 @@ __device__ __forceinline__ void lk_adj_bwd(const DevModel& M, const Mem& w, int 
       add_outer(Rb, ab, ax);
     }
   }
-  // spatial inertia: h = m c, Io = R Ic R^T + m(|c|^2 1 - c c^T), c = P + R com
-  const float m = __ldg(M.mass + i);
-  if (m != 0.f || __ldg(M.icom + 6 * i) != 0.f || __ldg(M.icom + 6 * i + 1) != 0.f || __ldg(M.icom + 6 * i + 2) != 0.f) {
-    const int osb = M.o_SIB + 12 * i;
-    const V3 hb = ld3(w, osb);
-    M33 G;
-#pragma unroll
-    for (int k = 0; k < 9; ++k) G.m[k] = w[osb + 3 + k];
-    const V3 com = cld3(M.com + 3 * i);
-    const V3 c = P + mul(R, com);
-    const float trG = G.m[0] + G.m[4] + G.m[8];
-    M33 Gs;   // G + G^T
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-      for (int b = 0; b < 3; ++b) Gs.m[3 * a + b] = G.m[3 * a + b] + G.m[3 * b + a];
-    const V3 cb = m * hb + m * (2.f * trG * c - mul(Gs, c));
-    const M33 GRI = mul(mul(Gs, R), com_inertia(M, i));
-#pragma unroll
-    for (int k = 0; k < 9; ++k) Rb.m[k] += GRI.m[k];
-    Pb = Pb + cb;
-    add_outer(Rb, cb, com);
-  }
   // joint transform
   const int s = __ldg(M.qs + i), p = __ldg(M.parent + i);
   if (jt == J_FREE) {   // the root origin is the reference point: no position cotangent here
@@ -1156,10 +1259,10 @@ __device__ __forceinline__ void lk_adj_bwd(const DevModel& M, const Mem& w, int 
 // Adjoint of the dynamics solve: given o_T = qdd_bar and the recomputed
 // substep (o_QDD holds the solved accelerations, o_M/o_LD the factor), add
 // -lambda^T dG/d(q, qd, a) to o_QB, o_QDB, o_ACTB with lambda = M^{-1} qdd_bar.
-template <int NM, class Mem>
-__device__ void st_dynamics_adj(const DevModel& M, const Mem& w, int lane, int nl) {
-  if constexpr (NM > 0) {
-    dense_solve(M, w, lane, nl, M.o_T, M.o_LAM);
+template <class Mem>
+__device__ void st_dynamics_adj(const DevModel& M, const Mem& w, int lane, int nl, int nm) {
+  if (nm > 0) {
+    dense_stored_solve_nm(M, w, lane, nl, nm, M.o_T, M.o_LAM);
   } else {
     for (int d = lane; d < M.nv; d += nl) w[M.o_B + d] = w[M.o_T + d];
     team_sync(nl);
@@ -1169,12 +1272,14 @@ __device__ void st_dynamics_adj(const DevModel& M, const Mem& w, int lane, int n
     for (int ii = __ldg(M.lvl_ptr + l) + lane; ii < __ldg(M.lvl_ptr + l + 1); ii += nl) {
       const int hd = __ldg(M.lvl_link + ii), tl = __ldg(M.chain_tail + hd);
       for (int i = hd;; i = chain_next(M, i)) {
-        lk_adj_fwd(M, w, i);
+        lk_adj_acc(M, w, i);
         if (i == tl) break;
       }
     }
     team_sync(nl);
   }
+  for (int i = lane; i < M.L; i += nl) lk_adj_local(M, w, i);
+  team_sync(nl);
   if (M.nseg > 0) {
     for (int sg = lane; sg < M.nseg; sg += nl) seg_adjoint(M, w, sg);
     team_sync(nl);
@@ -1216,11 +1321,11 @@ __device__ void st_dynamics_adj(const DevModel& M, const Mem& w, int lane, int n
 // One reverse substep: o_Q/o_QD hold the substep start state, o_QB/o_QDB the
 // cotangents of its end state; on return they hold the start-state cotangents,
 // and o_ACTB has accumulated the action cotangent.
-template <int NM, class Mem>
-__device__ void substep_adjoint(const DevModel& M, const Mem& w, int lane, int nl) {
-  substep_dynamics<NM>(M, w, lane, nl);     // recompute; the factor is kept for lambda
+template <class Mem>
+__device__ void substep_adjoint(const DevModel& M, const Mem& w, int lane, int nl, int nm) {
+  substep_dynamics(M, w, lane, nl, nm);     // recompute; the factor is kept for lambda
   st_integrate_adj(M, w, lane, nl);
-  st_dynamics_adj<NM>(M, w, lane, nl);
+  st_dynamics_adj(M, w, lane, nl, nm);
 }
 
 // non-finite check of the state (one lane)

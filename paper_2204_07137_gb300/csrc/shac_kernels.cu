@@ -12,7 +12,9 @@
 
 namespace shac {
 
-constexpr int BATCHED_BLOCK_MAX = 256;   // at most 8 warps per CTA
+// Register cap of the batched kernels; the host launches at most 8 warps per
+// CTA (8 x 32 x 168 registers fit an SM's 64 Ki).
+#define BATCHED_MAX_REGS 168
 
 // ------------------------------------------------------------------ PLAIN --
 
@@ -41,7 +43,7 @@ __global__ void k_plain_stage(PlainGroup g, int stage) {
       st_integrate_adj(M, w, 0, 1);
       break;
     case PS_ADJ_DYN:
-      st_dynamics_adj<0>(M, w, 0, 1);
+      st_dynamics_adj(M, w, 0, 1, 0);
       break;
     default:
       break;
@@ -193,9 +195,9 @@ __device__ __forceinline__ void setup_team(const BatchedArgs& a, const WorkItem&
 }
 
 // One work item of the forward window (all steps, all substeps).
-template <int NM>
 __device__ void forward_item(const BatchedArgs& a, const DevModel& M, const WorkItem& it, const SMem& w,
                              const Team& t) {
+  const int nm = a.dense_nm[it.group];
   const GroupIO& io = a.io.g[it.group];
   team_load(w, M.o_Q, a.q_in + io.q_off, M.nq, io.N, t.env, t.lane, t.nl);
   team_load(w, M.o_QD, a.qd_in + io.qd_off, M.nv, io.N, t.env, t.lane, t.nl);
@@ -208,7 +210,7 @@ __device__ void forward_item(const BatchedArgs& a, const DevModel& M, const Work
     clear_comp(M, w, t.lane, t.nl);
     team_sync(t.nl);
     for (int k = 0; k < M.K; ++k) {
-      substep_dynamics<NM>(M, w, t.lane, t.nl);
+      substep_dynamics(M, w, t.lane, t.nl, nm);
       st_integrate(M, w, t.lane, t.nl);
     }
     team_store(w, M.o_Q, a.q_out + (size_t)step * a.io.q_size + io.q_off, M.nq, io.N, t.env, t.lane, t.nl, t.active);
@@ -238,9 +240,9 @@ __device__ __forceinline__ void record_load(const SMem& w, const float* src, int
 // substeps are recomputed once from its checkpoint; every substep's record
 // (start state and forward intermediates, scratch [0, rec_floats)) is kept in
 // the workspace and reloaded by the reverse pass.
-template <int NM>
 __device__ void adjoint_item(const BatchedArgs& a, const DevModel& M, const WorkItem& it, const SMem& w,
                              const Team& t) {
+  const int nm = a.dense_nm[it.group];
   const GroupIO& io = a.io.g[it.group];
   const int REC = M.rec_floats;
   float* tape = a.tape + a.tape_off[it.group] + (size_t)(it.env0 + t.team) * ((size_t)M.K * REC);
@@ -254,7 +256,7 @@ __device__ void adjoint_item(const BatchedArgs& a, const DevModel& M, const Work
     clear_comp(M, w, t.lane, t.nl);
     team_sync(t.nl);
     for (int k = 0; k < M.K; ++k) {
-      substep_dynamics<NM>(M, w, t.lane, t.nl);
+      substep_dynamics(M, w, t.lane, t.nl, nm);
       float* rec = tape + (size_t)k * REC;
       for (int j = t.lane; j < REC; j += t.nl) rec[j] = w[j];
       team_sync(t.nl);
@@ -266,7 +268,7 @@ __device__ void adjoint_item(const BatchedArgs& a, const DevModel& M, const Work
       record_load(w, tape + (size_t)k * REC, REC, t.lane, t.nl);
       team_sync(t.nl);
       st_integrate_adj(M, w, t.lane, t.nl);
-      st_dynamics_adj<NM>(M, w, t.lane, t.nl);
+      st_dynamics_adj(M, w, t.lane, t.nl, nm);
     }
     team_store(w, M.o_ACTB, a.act_bar + (size_t)step * a.io.act_size + io.act_off, M.na, io.N, t.env, t.lane, t.nl,
                t.active);
@@ -282,10 +284,12 @@ __device__ void adjoint_item(const BatchedArgs& a, const DevModel& M, const Work
   team_store(w, M.o_QDB, a.qd0_bar + io.qd_off, M.nv, io.N, t.env, t.lane, t.nl, t.active);
 }
 
-// Persistent kernels: warps pull work items; each item dispatches on the
-// register capacity of its group's dense path (0 = shared-memory form).
+// Persistent kernels: warps pull work items (the dense path's register
+// capacity of each group is dispatched inside the substep).  168 registers
+// hold the adjoint's live state and the 32-row dense path without spills and
+// keep 12 warps per SM resident.
 template <bool ADJ>
-__global__ void __launch_bounds__(BATCHED_BLOCK_MAX) k_batched(BatchedArgs a) {
+__global__ void __maxnreg__(BATCHED_MAX_REGS) k_batched(BatchedArgs a) {
   extern __shared__ float smem[];
   __shared__ DevModel s_models[MAX_GROUPS];
   for (int g = threadIdx.x; g < a.n_groups; g += blockDim.x) s_models[g] = a.models[g];
@@ -299,19 +303,8 @@ __global__ void __launch_bounds__(BATCHED_BLOCK_MAX) k_batched(BatchedArgs a) {
     Team t;
     setup_team(a, it, t);
     SMem w{wsm + (size_t)t.team * a.env_stride[it.group]};
-    switch (a.dense_nm[it.group]) {
-      case 8:
-        if (ADJ) adjoint_item<8>(a, M, it, w, t); else forward_item<8>(a, M, it, w, t);
-        break;
-      case 16:
-        if (ADJ) adjoint_item<16>(a, M, it, w, t); else forward_item<16>(a, M, it, w, t);
-        break;
-      case 32:
-        if (ADJ) adjoint_item<32>(a, M, it, w, t); else forward_item<32>(a, M, it, w, t);
-        break;
-      default:
-        if (ADJ) adjoint_item<0>(a, M, it, w, t); else forward_item<0>(a, M, it, w, t);
-    }
+    if (ADJ) adjoint_item(a, M, it, w, t);
+    else forward_item(a, M, it, w, t);
     __syncwarp();
   }
 }

@@ -1,0 +1,55 @@
+"""Launch shapes of the batched kernels from a fresh CUDA context.
+
+Shared memory per CTA grows with the warps per CTA; between 44 and 48 KB of
+dynamic shared memory the kernels' static part pushes a CTA over the default
+48 KB and the opt-in attribute is required.  Attributes persist in a process,
+so the sweep runs in a fresh child process, smallest CTA first."""
+import os
+import subprocess
+import sys
+
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+CHILD = r"""
+import sys, numpy as np, torch
+sys.path.insert(0, sys.argv[1])
+from paper_2204_07137_gb300 import inputs as I
+from paper_2204_07137_gb300.sim import Simulator
+T = lambda x: torch.from_numpy(np.ascontiguousarray(np.asarray(x, np.float32).reshape(-1))).cuda()
+for name in ("ant", "humanoid", "mtu"):
+    m = getattr(I, name)()
+    for warps in range(1, 9):
+        N = 8 * warps + 3
+        sim = Simulator([(m, N)], form="batched", h_max=1)
+        sim.set_launch(0, 0, warps)
+        lanes, w_used = sim.get_launch(0)
+        q0, qd0 = I.initial_state(m, N, 0)
+        act = T(I.window_actions(m, N, 1, 0)).view(1, -1)
+        qt, qdt, r = sim.window_forward(T(q0), T(qd0), act)
+        g = sim.window_adjoint(qt, qdt, act, torch.ones(1, N, device="cuda"),
+                               torch.zeros_like(qt), torch.zeros_like(qdt))
+        torch.cuda.synchronize()
+        assert all(torch.isfinite(x).all() for x in (qt, qdt, r) + tuple(g)), (name, warps)
+        print(name, warps, lanes, w_used)
+print("ok")
+"""
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2204_07137_gb300 import build
+    build.build()
+
+
+def test_every_cta_size_launches_in_a_fresh_context():
+    out = subprocess.run([sys.executable, "-c", CHILD, ROOT], capture_output=True, text=True, timeout=600)
+    assert out.returncode == 0, out.stdout[-2000:] + out.stderr[-4000:]
+    assert out.stdout.strip().endswith("ok")

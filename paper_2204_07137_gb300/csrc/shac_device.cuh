@@ -264,38 +264,78 @@ __device__ __forceinline__ void lk_muscle_wrench(const DevModel& M, const Mem& w
 // sweeps) or child-first (leaves-first sweeps); one team barrier per chain level.
 __device__ __forceinline__ int chain_next(const DevModel& M, int i) { return __ldg(M.ch_idx + __ldg(M.ch_ptr + i)); }
 
-// Sweep 1 is split in two passes.  The root-first pass carries what flows
-// down the tree (lk_kin); everything else a link needs is local to it and
-// runs with one lane per link for all links at once (lk_local), so the
-// sequential critical path holds only the light kinematic recursion.
+// Sweep 1 is split into passes.  Only what flows down the tree - the world
+// pose, velocity and acceleration of the parent - is computed in the
+// root-first pass, and a lane walking a chain keeps the parent's values in
+// registers (KinCarry).  Everything local to a link runs with one lane per
+// link for all links at once: the joint's own transform before the
+// root-first pass (lk_joint_local), the inertia, contacts and local force
+// after it (lk_local).
 //
-// lk_kin: forward kinematics from the parent (rotation R_i, origin P_i), the
-// motion-subspace columns (revolute (a, P x a), prismatic (0, a), free
-// (R e_k, P x R e_k) for the body rates and (0, R e_k) for v_body), the
-// velocity V_i = V_p + u_i and the Newton-Euler acceleration
-// A_i = A_p + V_i x u_i with qdd = 0 (gravity enters as the base acceleration -g).
+// lk_joint_local: pose of link i in its parent's frame (joint frame times
+// joint motion: Rot(axis, q) for revolute, q axis for prismatic; the free
+// root's pose from its quaternion), written to o_R / o_P of link i.
 template <class Mem>
-__device__ __forceinline__ void lk_kin(const DevModel& M, const Mem& w, int i) {
-  const int jt = __ldg(M.jtype + i), s = __ldg(M.qs + i), p = __ldg(M.parent + i);
-  const int d0 = __ldg(M.ds + i), nd = __ldg(M.nd + i);
+__device__ __forceinline__ void lk_joint_local(const DevModel& M, const Mem& w, int i) {
+  const int jt = __ldg(M.jtype + i), s = __ldg(M.qs + i);
   M33 R;
   V3 P;
-  const V3 ax = cld3(M.axis + 3 * i);
   if (jt == J_FREE) {
     R = quat_to_R(w[M.o_Q + s + 3], w[M.o_Q + s + 4], w[M.o_Q + s + 5], w[M.o_Q + s + 6]);
     P = v3(0.f, 0.f, 0.f);
   } else {
-    M33 Rj = cldm(M.jrot + 9 * i);
-    V3 Pj = cld3(M.jpos + 3 * i);
-    if (jt == J_REV) Rj = mul(Rj, axis_angle(ax, w[M.o_Q + s]));   // independent of the parent
-    if (p >= 0) {
-      const M33 Rp = ldm(w, M.o_R + 9 * p);
-      Pj = ld3(w, M.o_P + 3 * p) + mul(Rp, Pj);
-      Rj = mul(Rp, Rj);
-    }
-    R = Rj;
-    P = Pj;
-    if (jt == J_PRIS) P = Pj + w[M.o_Q + s] * mul(Rj, ax);
+    R = cldm(M.jrot + 9 * i);
+    P = cld3(M.jpos + 3 * i);
+    const V3 ax = cld3(M.axis + 3 * i);
+    if (jt == J_REV) R = mul(R, axis_angle(ax, w[M.o_Q + s]));
+    else if (jt == J_PRIS) P = P + w[M.o_Q + s] * mul(R, ax);
+  }
+  stm(w, M.o_R + 9 * i, R);
+  st3(w, M.o_P + 3 * i, P);
+}
+
+// World pose, velocity and acceleration carried from a link to its child.
+struct KinCarry {
+  M33 R;
+  V3 P, Vw, Vv, aw, av;
+};
+
+// Parent state of a chain head (the tree root: identity frame at rest, with
+// gravity as the base acceleration -g).
+template <class Mem>
+__device__ __forceinline__ void kin_parent(const DevModel& M, const Mem& w, int p, KinCarry& c) {
+  if (p >= 0) {
+    c.R = ldm(w, M.o_R + 9 * p);
+    c.P = ld3(w, M.o_P + 3 * p);
+    c.Vw = ld3(w, M.o_V + 6 * p); c.Vv = ld3(w, M.o_V + 6 * p + 3);
+    c.aw = ld3(w, M.o_A + 6 * p); c.av = ld3(w, M.o_A + 6 * p + 3);
+  } else {
+    c.Vw = c.Vv = c.aw = v3(0.f, 0.f, 0.f);
+    c.av = v3(-M.grav[0], -M.grav[1], -M.grav[2]);
+  }
+}
+
+// lk_kin: world pose R_i = R_p R_local, P_i = P_p + R_p P_local (the root and
+// a free joint: the local pose), the motion-subspace columns (revolute
+// (a, P x a), prismatic (0, a), free (R e_k, P x R e_k) for the body rates and
+// (0, R e_k) for v_body), the velocity V_i = V_p + u_i and the Newton-Euler
+// acceleration A_i = A_p + V_i x u_i with qdd = 0.  c holds the parent's state
+// on entry and link i's on return.
+template <class Mem>
+__device__ __forceinline__ void lk_kin(const DevModel& M, const Mem& w, int i, KinCarry& c) {
+  const int jt = __ldg(M.jtype + i), p = __ldg(M.parent + i);
+  const int d0 = __ldg(M.ds + i), nd = __ldg(M.nd + i);
+  const V3 ax = cld3(M.axis + 3 * i);
+  const M33 Rl = ldm(w, M.o_R + 9 * i);
+  const V3 Pl = ld3(w, M.o_P + 3 * i);
+  M33 R;
+  V3 P;
+  if (jt == J_FREE || p < 0) {
+    R = Rl;
+    P = Pl;
+  } else {
+    R = mul(c.R, Rl);
+    P = c.P + mul(c.R, Pl);
   }
   stm(w, M.o_R + 9 * i, R);
   st3(w, M.o_P + 3 * i, P);
@@ -316,17 +356,12 @@ __device__ __forceinline__ void lk_kin(const DevModel& M, const Mem& w, int i) {
     uw = uw + qd * sw;
     uv = uv + qd * sv;
   }
-  V3 Vw = uw, Vv = uv, aw, av;
-  if (p >= 0) {
-    Vw = Vw + ld3(w, M.o_V + 6 * p); Vv = Vv + ld3(w, M.o_V + 6 * p + 3);
-    aw = ld3(w, M.o_A + 6 * p); av = ld3(w, M.o_A + 6 * p + 3);
-  } else {
-    aw = v3(0.f, 0.f, 0.f); av = v3(-M.grav[0], -M.grav[1], -M.grav[2]);
-  }
-  aw = aw + cross(Vw, uw);
-  av = av + cross(Vw, uv) + cross(Vv, uw);
+  const V3 Vw = c.Vw + uw, Vv = c.Vv + uv;
+  const V3 aw = c.aw + cross(Vw, uw);
+  const V3 av = c.av + cross(Vw, uv) + cross(Vv, uw);
   st3(w, M.o_V + 6 * i, Vw); st3(w, M.o_V + 6 * i + 3, Vv);
   st3(w, M.o_A + 6 * i, aw); st3(w, M.o_A + 6 * i + 3, av);
+  c.R = R; c.P = P; c.Vw = Vw; c.Vv = Vv; c.aw = aw; c.av = av;
 }
 
 // lk_local: the spatial inertia about the reference point (m, h = m c, Io),
@@ -399,17 +434,21 @@ __device__ __forceinline__ void lk_local(const DevModel& M, const Mem& w, int i)
   st3(w, M.o_F + 6 * i + 3, ff);
 }
 
-// Sweep 1: root first the kinematics, subspaces, velocities and Newton-Euler
-// accelerations (qdd = 0) of every link; then, one lane per link, the
-// inertias, contact forces and local forces; then the muscle wrenches (their
-// segments span two links).
+// Sweep 1: one lane per link the joint transforms; root first the world
+// poses, subspaces, velocities and Newton-Euler accelerations (qdd = 0) of
+// every link; one lane per link the inertias, contact forces and local
+// forces; then the muscle wrenches (their segments span two links).
 template <class Mem>
 __device__ void sw_forward(const DevModel& M, const Mem& w, int lane, int nl) {
+  for (int i = lane; i < M.L; i += nl) lk_joint_local(M, w, i);
+  team_sync(nl);
   for (int l = 0; l < M.nlev; ++l) {
     for (int ii = __ldg(M.lvl_ptr + l) + lane; ii < __ldg(M.lvl_ptr + l + 1); ii += nl) {
       const int hd = __ldg(M.lvl_link + ii), tl = __ldg(M.chain_tail + hd);
+      KinCarry c;
+      kin_parent(M, w, __ldg(M.parent + hd), c);
       for (int i = hd;; i = chain_next(M, i)) {
-        lk_kin(M, w, i);
+        lk_kin(M, w, i, c);
         if (i == tl) break;
       }
     }
@@ -432,42 +471,57 @@ __device__ void sw_forward(const DevModel& M, const Mem& w, int lane, int nl) {
   }
 }
 
-// F_i += sum_children F_c (total forces) and, with_ic, the composite inertia
-// Ic_i = I_i + sum_children Ic_c (CRBA part 1).
+// Total force and composite inertia of the link a chain walk just finished,
+// carried in registers to its parent (the next link up the chain).
+struct GatherCarry {
+  V3 fn, ff;
+  float ic[10];
+};
+
+// F_i += sum_children F_c (total forces) and the composite inertia
+// Ic_i = I_i + sum_children Ic_c (CRBA part 1).  Inside a chain the only child
+// is the link walked before (carried in g); the chain's tail reads its
+// children from scratch.
 template <class Mem>
-__device__ __forceinline__ void lk_gather(const DevModel& M, const Mem& w, int i, bool with_ic) {
-  const int c0 = __ldg(M.ch_ptr + i), c1 = __ldg(M.ch_ptr + i + 1);
+__device__ __forceinline__ void lk_gather(const DevModel& M, const Mem& w, int i, bool tail, GatherCarry& g) {
   V3 fn = ld3(w, M.o_F + 6 * i), ff = ld3(w, M.o_F + 6 * i + 3);
   float ic[10];
-  if (with_ic) {
 #pragma unroll
-    for (int k = 0; k < 10; ++k) ic[k] = w[M.o_SI + 10 * i + k];
-  }
-  for (int kk = c0; kk < c1; ++kk) {
-    const int c = __ldg(M.ch_idx + kk);
-    fn = fn + ld3(w, M.o_F + 6 * c);
-    ff = ff + ld3(w, M.o_F + 6 * c + 3);
-    if (with_ic) {
+  for (int k = 0; k < 10; ++k) ic[k] = w[M.o_SI + 10 * i + k];
+  if (tail) {
+    const int c0 = __ldg(M.ch_ptr + i), c1 = __ldg(M.ch_ptr + i + 1);
+    for (int kk = c0; kk < c1; ++kk) {
+      const int c = __ldg(M.ch_idx + kk);
+      fn = fn + ld3(w, M.o_F + 6 * c);
+      ff = ff + ld3(w, M.o_F + 6 * c + 3);
 #pragma unroll
       for (int k = 0; k < 10; ++k) ic[k] += w[M.o_IC + 10 * c + k];
     }
+  } else {
+    fn = fn + g.fn;
+    ff = ff + g.ff;
+#pragma unroll
+    for (int k = 0; k < 10; ++k) ic[k] += g.ic[k];
   }
   st3(w, M.o_F + 6 * i, fn);
   st3(w, M.o_F + 6 * i + 3, ff);
-  if (with_ic) {
 #pragma unroll
-    for (int k = 0; k < 10; ++k) w[M.o_IC + 10 * i + k] = ic[k];
-  }
+  for (int k = 0; k < 10; ++k) w[M.o_IC + 10 * i + k] = ic[k];
+  g.fn = fn;
+  g.ff = ff;
+#pragma unroll
+  for (int k = 0; k < 10; ++k) g.ic[k] = ic[k];
 }
 
-// Sweep 2, leaves first: total forces (and composite inertias).
+// Sweep 2, leaves first: total forces and composite inertias.
 template <class Mem>
-__device__ void sw_gather(const DevModel& M, const Mem& w, int lane, int nl, bool with_ic) {
+__device__ void sw_gather(const DevModel& M, const Mem& w, int lane, int nl) {
   for (int l = M.nlev - 1; l >= 0; --l) {
     for (int ii = __ldg(M.lvl_ptr + l) + lane; ii < __ldg(M.lvl_ptr + l + 1); ii += nl) {
-      const int hd = __ldg(M.lvl_link + ii);
-      for (int i = __ldg(M.chain_tail + hd);; i = __ldg(M.parent + i)) {
-        lk_gather(M, w, i, with_ic);
+      const int hd = __ldg(M.lvl_link + ii), tl = __ldg(M.chain_tail + hd);
+      GatherCarry g;
+      for (int i = tl;; i = __ldg(M.parent + i)) {
+        lk_gather(M, w, i, i == tl, g);
         if (i == hd) break;
       }
     }
@@ -806,7 +860,7 @@ __device__ __forceinline__ void dense_stored_solve_nm(const DevModel& M, const M
 template <class Mem>
 __device__ void substep_dynamics(const DevModel& M, const Mem& w, int lane, int nl, int nm) {
   sw_forward(M, w, lane, nl);
-  sw_gather(M, w, lane, nl, true);
+  sw_gather(M, w, lane, nl);
   if (nm > 0) {
     dense_substep_nm(M, w, lane, nl, nm, lane < M.nv ? dof_rhs(M, w, lane) : 0.f);
   } else {
@@ -939,18 +993,26 @@ __device__ __forceinline__ void add_outer(M33& A, V3 a, V3 b) {   // A += a b^T
 //
 // lk_adj_acc, root first: the accelerations A_i = A_p + sum_{d in i} S_d qdd_d
 // + V_i x u_i with the solved qdd, and the force cotangent
-// F_bar_i = F_bar_p + sum_{d in i} w_d S_d.
+// F_bar_i = F_bar_p + sum_{d in i} w_d S_d.  c carries (A, F_bar) of the
+// parent in registers on entry and link i's on return.
+struct AccCarry {
+  V3 aw, av, nb, fb;
+};
 template <class Mem>
-__device__ __forceinline__ void lk_adj_acc(const DevModel& M, const Mem& w, int i) {
-  const int p = __ldg(M.parent + i), d0 = __ldg(M.ds + i), nd = __ldg(M.nd + i);
-  const V3 Vw = ld3(w, M.o_V + 6 * i), Vv = ld3(w, M.o_V + 6 * i + 3);
-  V3 aw, av, nb = v3(0.f, 0.f, 0.f), fb = v3(0.f, 0.f, 0.f);
+__device__ __forceinline__ void acc_parent(const DevModel& M, const Mem& w, int p, AccCarry& c) {
   if (p >= 0) {
-    aw = ld3(w, M.o_A + 6 * p); av = ld3(w, M.o_A + 6 * p + 3);
-    nb = ld3(w, M.o_FB + 6 * p); fb = ld3(w, M.o_FB + 6 * p + 3);
+    c.aw = ld3(w, M.o_A + 6 * p); c.av = ld3(w, M.o_A + 6 * p + 3);
+    c.nb = ld3(w, M.o_FB + 6 * p); c.fb = ld3(w, M.o_FB + 6 * p + 3);
   } else {
-    aw = v3(0.f, 0.f, 0.f); av = v3(-M.grav[0], -M.grav[1], -M.grav[2]);
+    c.aw = c.nb = c.fb = v3(0.f, 0.f, 0.f);
+    c.av = v3(-M.grav[0], -M.grav[1], -M.grav[2]);
   }
+}
+template <class Mem>
+__device__ __forceinline__ void lk_adj_acc(const DevModel& M, const Mem& w, int i, AccCarry& c) {
+  const int d0 = __ldg(M.ds + i), nd = __ldg(M.nd + i);
+  const V3 Vw = ld3(w, M.o_V + 6 * i), Vv = ld3(w, M.o_V + 6 * i + 3);
+  V3 aw = c.aw, av = c.av, nb = c.nb, fb = c.fb;
   V3 uw = v3(0.f, 0.f, 0.f), uv = v3(0.f, 0.f, 0.f);
   for (int d = d0; d < d0 + nd; ++d) {
     const V3 sw = ld3(w, M.o_S + 6 * d), sv = ld3(w, M.o_S + 6 * d + 3);
@@ -963,6 +1025,7 @@ __device__ __forceinline__ void lk_adj_acc(const DevModel& M, const Mem& w, int 
   av = av + cross(Vw, uv) + cross(Vv, uw);
   st3(w, M.o_A + 6 * i, aw); st3(w, M.o_A + 6 * i + 3, av);
   st3(w, M.o_FB + 6 * i, nb); st3(w, M.o_FB + 6 * i + 3, fb);
+  c.aw = aw; c.av = av; c.nb = nb; c.fb = fb;
 }
 
 // Cotangent of the spatial inertia from y = I x (y_bar given): h_bar and the
@@ -1106,6 +1169,10 @@ __device__ __forceinline__ void lk_adj_local(const DevModel& M, const Mem& w, in
   st3(w, M.o_VB + 6 * i + 3, vvb);
   st3(w, M.o_PB + 3 * i, Pb);
   stm(w, M.o_RB + 9 * i, Rb);
+  // joint-local rotation R_local = jrot Rot(axis, q) of a revolute joint with
+  // a parent, kept in o_TP of link i until the leaves-first sweep replaces it
+  if (jt == J_REV && __ldg(M.parent + i) >= 0)
+    stm(w, M.o_TP + 12 * i, mul(cldm(M.jrot + 9 * i), axis_angle(cld3(M.axis + 3 * i), w[M.o_Q + __ldg(M.qs + i)])));
 }
 
 // Reverse of one muscle segment: cotangents of both via points and of the
@@ -1139,31 +1206,51 @@ __device__ __forceinline__ void seg_adjoint(const DevModel& M, const Mem& w, int
   st3(w, M.o_ITB + 10 * e1, x1b);
 }
 
+// Children's contributions carried up a chain in registers: subtree sums of
+// the total force and of A_bar, the child's V_bar and its cotangent of this
+// link's pose (what o_TP holds for a chain head).
+struct BwdCarry {
+  V3 Fn, Ff, an, af, vw, vv, tP;
+  M33 tR;
+};
+
 // Adjoint sweep 2 (leaves first) at link i: gather the children (total
-// forces, A_bar, V_bar, kinematic cotangents), reverse the Newton-Euler
-// accelerations and velocities, the motion subspaces and the joint transform
-// (forward kinematics).  The inertia's share of the pose cotangents was added
-// by lk_adj_local.
+// forces, A_bar, V_bar, kinematic cotangents; inside a chain the only child
+// is the link walked before, carried in g), reverse the Newton-Euler
+// accelerations and velocities and the motion subspaces, and pass the pose
+// cotangent through the joint transform to the parent (R_p_bar, P_p_bar in
+// o_TP).  The inertia's share of the pose cotangents was added by
+// lk_adj_local; the joint's own q_bar is taken after the sweep (lk_adj_qbar)
+// from the final R_bar, P_bar left in o_RB, o_PB.
 template <class Mem>
-__device__ __forceinline__ void lk_adj_bwd(const DevModel& M, const Mem& w, int i) {
-  const int c0 = __ldg(M.ch_ptr + i), c1 = __ldg(M.ch_ptr + i + 1);
+__device__ __forceinline__ void lk_adj_bwd(const DevModel& M, const Mem& w, int i, bool tail, BwdCarry& g) {
   V3 Fn = ld3(w, M.o_F + 6 * i), Ff = ld3(w, M.o_F + 6 * i + 3);
   V3 an = ld3(w, M.o_AB + 6 * i), af = ld3(w, M.o_AB + 6 * i + 3);
   V3 vw = ld3(w, M.o_VB + 6 * i), vv = ld3(w, M.o_VB + 6 * i + 3);
   M33 Rb = ldm(w, M.o_RB + 9 * i);
   V3 Pb = ld3(w, M.o_PB + 3 * i);
   V3 cvw = v3(0.f, 0.f, 0.f), cvv = v3(0.f, 0.f, 0.f);
-  for (int k = c0; k < c1; ++k) {
-    const int c = __ldg(M.ch_idx + k);
-    Fn = Fn + ld3(w, M.o_F + 6 * c);
-    Ff = Ff + ld3(w, M.o_F + 6 * c + 3);
-    an = an + ld3(w, M.o_AB + 6 * c);
-    af = af + ld3(w, M.o_AB + 6 * c + 3);
-    cvw = cvw + ld3(w, M.o_VB + 6 * c);
-    cvv = cvv + ld3(w, M.o_VB + 6 * c + 3);
+  if (tail) {
+    const int c0 = __ldg(M.ch_ptr + i), c1 = __ldg(M.ch_ptr + i + 1);
+    for (int k = c0; k < c1; ++k) {
+      const int c = __ldg(M.ch_idx + k);
+      Fn = Fn + ld3(w, M.o_F + 6 * c);
+      Ff = Ff + ld3(w, M.o_F + 6 * c + 3);
+      an = an + ld3(w, M.o_AB + 6 * c);
+      af = af + ld3(w, M.o_AB + 6 * c + 3);
+      cvw = cvw + ld3(w, M.o_VB + 6 * c);
+      cvv = cvv + ld3(w, M.o_VB + 6 * c + 3);
 #pragma unroll
-    for (int t = 0; t < 9; ++t) Rb.m[t] += w[M.o_TP + 12 * c + t];
-    Pb = Pb + ld3(w, M.o_TP + 12 * c + 9);
+      for (int t = 0; t < 9; ++t) Rb.m[t] += w[M.o_TP + 12 * c + t];
+      Pb = Pb + ld3(w, M.o_TP + 12 * c + 9);
+    }
+  } else {
+    Fn = Fn + g.Fn; Ff = Ff + g.Ff;
+    an = an + g.an; af = af + g.af;
+    cvw = g.vw; cvv = g.vv;
+#pragma unroll
+    for (int t = 0; t < 9; ++t) Rb.m[t] += g.tR.m[t];
+    Pb = Pb + g.tP;
   }
   st3(w, M.o_F + 6 * i, Fn);
   st3(w, M.o_F + 6 * i + 3, Ff);
@@ -1212,23 +1299,48 @@ __device__ __forceinline__ void lk_adj_bwd(const DevModel& M, const Mem& w, int 
       add_outer(Rb, ab, ax);
     }
   }
-  // joint transform
-  const int s = __ldg(M.qs + i), p = __ldg(M.parent + i);
+  stm(w, M.o_RB + 9 * i, Rb);
+  st3(w, M.o_PB + 3 * i, Pb);
+  g.Fn = Fn; g.Ff = Ff; g.an = an; g.af = af; g.vw = vw; g.vv = vv;
+  const int p = __ldg(M.parent + i);
+  if (p >= 0 && jt != J_FREE) {
+    // Rj = Rp jrot (joint frame in world), R = Rj Rot(ax, q), Pj = Pp + Rp jpos
+    M33 tp;
+    if (jt == J_REV) {
+      tp = mulBT(Rb, ldm(w, M.o_TP + 12 * i));   // R_p_bar = R_bar R_local^T
+    } else {
+      M33 Rjb = Rb;
+      if (jt == J_PRIS) add_outer(Rjb, w[M.o_Q + __ldg(M.qs + i)] * Pb, ax);   // P = Pj + q Rj ax
+      tp = mulBT(Rjb, cldm(M.jrot + 9 * i));
+    }
+    add_outer(tp, Pb, cld3(M.jpos + 3 * i));
+    stm(w, M.o_TP + 12 * i, tp);
+    st3(w, M.o_TP + 12 * i + 9, Pb);
+    g.tR = tp;
+    g.tP = Pb;
+  }
+}
+
+// q_bar of link i's joint from its final pose cotangents: revolute
+// dR/dq = [a]x R with a = R ax; prismatic dP/dq = a; free root: the
+// quaternion's share through R(quat), and the root height receives every
+// contact depth's cotangent (depth = x.z + root height).
+template <class Mem>
+__device__ __forceinline__ void lk_adj_qbar(const DevModel& M, const Mem& w, int i) {
+  const int jt = __ldg(M.jtype + i), s = __ldg(M.qs + i);
+  const M33 Rb = ldm(w, M.o_RB + 9 * i);
   if (jt == J_FREE) {   // the root origin is the reference point: no position cotangent here
     float xb = 0.f, yb = 0.f, zb = 0.f, wb = 0.f;
     quat_to_R_adj(w[M.o_Q + s + 3], w[M.o_Q + s + 4], w[M.o_Q + s + 5], w[M.o_Q + s + 6], Rb, xb, yb, zb, wb);
     w[M.o_QB + s + 3] += xb; w[M.o_QB + s + 4] += yb; w[M.o_QB + s + 5] += zb; w[M.o_QB + s + 6] += wb;
-    if (M.root_free && i == 0) {   // depth = x.z + root height: the root height gets every d_bar
+    if (M.root_free && i == 0) {
       float sd = 0.f;
       for (int c = 0; c < M.nc; ++c) sd += w[M.o_ITB + 10 * c + 9];
       w[M.o_QB + 2] += sd;
     }
-    return;
-  }
-  M33 Rjb;   // cotangent of Rj (joint frame in world)
-  if (jt == J_REV) {
-    // R = Rj Rot(ax, q); dR/dq = [a]x R with a = R ax
-    const V3 a = mul(R, ax);
+  } else if (jt == J_REV) {
+    const M33 R = ldm(w, M.o_R + 9 * i);
+    const V3 a = mul(R, cld3(M.axis + 3 * i));
     float qb = 0.f;
 #pragma unroll
     for (int cc = 0; cc < 3; ++cc) {
@@ -1236,23 +1348,9 @@ __device__ __forceinline__ void lk_adj_bwd(const DevModel& M, const Mem& w, int 
       qb += Rb.m[cc] * dcol.x + Rb.m[3 + cc] * dcol.y + Rb.m[6 + cc] * dcol.z;
     }
     w[M.o_QB + s] += qb;
-    Rjb = mulBT(Rb, axis_angle(ax, w[M.o_Q + s]));
   } else if (jt == J_PRIS) {
-    // P = Pj + q Rj ax
-    const V3 a = mul(R, ax);
-    w[M.o_QB + s] += dot(Pb, a);
-    Rjb = Rb;
-    add_outer(Rjb, w[M.o_Q + s] * Pb, ax);
-  } else {
-    Rjb = Rb;
-  }
-  if (p >= 0) {
-    // Rj = Rp jrot, Pj = Pp + Rp jpos
-    M33 tp = mulBT(Rjb, cldm(M.jrot + 9 * i));
-    add_outer(tp, Pb, cld3(M.jpos + 3 * i));
-#pragma unroll
-    for (int t = 0; t < 9; ++t) w[M.o_TP + 12 * i + t] = tp.m[t];
-    st3(w, M.o_TP + 12 * i + 9, Pb);
+    const M33 R = ldm(w, M.o_R + 9 * i);
+    w[M.o_QB + s] += dot(ld3(w, M.o_PB + 3 * i), mul(R, cld3(M.axis + 3 * i)));
   }
 }
 
@@ -1271,8 +1369,10 @@ __device__ void st_dynamics_adj(const DevModel& M, const Mem& w, int lane, int n
   for (int l = 0; l < M.nlev; ++l) {
     for (int ii = __ldg(M.lvl_ptr + l) + lane; ii < __ldg(M.lvl_ptr + l + 1); ii += nl) {
       const int hd = __ldg(M.lvl_link + ii), tl = __ldg(M.chain_tail + hd);
+      AccCarry c;
+      acc_parent(M, w, __ldg(M.parent + hd), c);
       for (int i = hd;; i = chain_next(M, i)) {
-        lk_adj_acc(M, w, i);
+        lk_adj_acc(M, w, i, c);
         if (i == tl) break;
       }
     }
@@ -1308,14 +1408,17 @@ __device__ void st_dynamics_adj(const DevModel& M, const Mem& w, int lane, int n
   }
   for (int l = M.nlev - 1; l >= 0; --l) {
     for (int ii = __ldg(M.lvl_ptr + l) + lane; ii < __ldg(M.lvl_ptr + l + 1); ii += nl) {
-      const int hd = __ldg(M.lvl_link + ii);
-      for (int i = __ldg(M.chain_tail + hd);; i = __ldg(M.parent + i)) {
-        lk_adj_bwd(M, w, i);
+      const int hd = __ldg(M.lvl_link + ii), tl = __ldg(M.chain_tail + hd);
+      BwdCarry g;
+      for (int i = tl;; i = __ldg(M.parent + i)) {
+        lk_adj_bwd(M, w, i, i == tl, g);
         if (i == hd) break;
       }
     }
     team_sync(nl);
   }
+  for (int i = lane; i < M.L; i += nl) lk_adj_qbar(M, w, i);
+  team_sync(nl);
 }
 
 // One reverse substep: o_Q/o_QD hold the substep start state, o_QB/o_QDB the

@@ -12,9 +12,12 @@
 
 namespace shac {
 
-// Register cap of the batched kernels; the host launches at most 8 warps per
-// CTA (8 x 32 x 168 registers fit an SM's 64 Ki).
-#define BATCHED_MAX_REGS 168
+// Register caps of the batched kernels (forward, adjoint): the live state of
+// the chain carries and of the 32-row dense path fits without spills; the
+// host launches at most 8 warps per CTA (8 x 32 x 200 registers fit an SM's
+// 64 Ki).
+#define BATCHED_REGS_FORWARD 184
+#define BATCHED_REGS_ADJOINT 200
 
 // ------------------------------------------------------------------ PLAIN --
 
@@ -28,7 +31,7 @@ __global__ void k_plain_stage(PlainGroup g, int stage) {
       sw_forward(M, w, 0, 1);
       break;
     case PS_BIAS:
-      sw_gather(M, w, 0, 1, true); st_rhs(M, w, 0, 1);
+      sw_gather(M, w, 0, 1); st_rhs(M, w, 0, 1);
       break;
     case PS_CRBA:
       st_mass_rows(M, w, 0, 1);
@@ -285,11 +288,9 @@ __device__ void adjoint_item(const BatchedArgs& a, const DevModel& M, const Work
 }
 
 // Persistent kernels: warps pull work items (the dense path's register
-// capacity of each group is dispatched inside the substep).  168 registers
-// hold the adjoint's live state and the 32-row dense path without spills and
-// keep 12 warps per SM resident.
+// capacity of each group is dispatched inside the substep).
 template <bool ADJ>
-__global__ void __maxnreg__(BATCHED_MAX_REGS) k_batched(BatchedArgs a) {
+__global__ void __maxnreg__(ADJ ? BATCHED_REGS_ADJOINT : BATCHED_REGS_FORWARD) k_batched(BatchedArgs a) {
   extern __shared__ float smem[];
   __shared__ DevModel s_models[MAX_GROUPS];
   for (int g = threadIdx.x; g < a.n_groups; g += blockDim.x) s_models[g] = a.models[g];

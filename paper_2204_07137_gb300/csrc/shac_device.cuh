@@ -340,21 +340,24 @@ __device__ __forceinline__ void lk_kin(const DevModel& M, const Mem& w, int i, K
   stm(w, M.o_R + 9 * i, R);
   st3(w, M.o_P + 3 * i, P);
   V3 uw = v3(0.f, 0.f, 0.f), uv = v3(0.f, 0.f, 0.f);
-  for (int k = 0; k < nd; ++k) {
-    V3 sw, sv;
-    if (jt == J_FREE) {
-      if (k < 3) { sw = col(R, k); sv = cross(P, sw); }
-      else { sw = v3(0.f, 0.f, 0.f); sv = col(R, k - 3); }
-    } else {
-      const V3 a = mul(R, ax);
-      if (jt == J_REV) { sw = a; sv = cross(P, a); }
-      else { sw = v3(0.f, 0.f, 0.f); sv = a; }
-    }
+  auto subspace = [&](int k, V3 sw, V3 sv) {
     st3(w, M.o_S + 6 * (d0 + k), sw);
     st3(w, M.o_S + 6 * (d0 + k) + 3, sv);
     const float qd = w[M.o_QD + d0 + k];
     uw = uw + qd * sw;
     uv = uv + qd * sv;
+  };
+  // DOF counts are fixed by the joint type (free 6, revolute / prismatic 1,
+  // fixed 0), so every column index below is a compile-time constant
+  if (jt == J_FREE) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) subspace(k, col(R, k), cross(P, col(R, k)));
+#pragma unroll
+    for (int k = 0; k < 3; ++k) subspace(3 + k, v3(0.f, 0.f, 0.f), col(R, k));
+  } else if (nd == 1) {
+    const V3 a = mul(R, ax);
+    if (jt == J_REV) subspace(0, a, cross(P, a));
+    else subspace(0, v3(0.f, 0.f, 0.f), a);
   }
   const V3 Vw = c.Vw + uw, Vv = c.Vv + uv;
   const V3 aw = c.aw + cross(Vw, uw);
@@ -1271,33 +1274,44 @@ __device__ __forceinline__ void lk_adj_bwd(const DevModel& M, const Mem& w, int 
   const V3 P = ld3(w, M.o_P + 3 * i);
   const int jt = __ldg(M.jtype + i), d0 = __ldg(M.ds + i), nd = __ldg(M.nd + i);
   const V3 ax = cld3(M.axis + 3 * i);
-  for (int d = d0; d < d0 + nd; ++d) {
+  // per DOF: tau = S^T F_total gives qd_bar and the subspace cotangents
+  // (sbw, sbv); DOF counts are fixed by the joint type, so the column index
+  // of a free joint is a compile-time constant
+  auto dof_terms = [&](int k, V3& sbw, V3& sbv) {
+    const int d = d0 + k;
     const float wd = -w[M.o_LAM + d], qdd = w[M.o_QDD + d], qd = w[M.o_QD + d];
     const V3 sw = ld3(w, M.o_S + 6 * d), sv = ld3(w, M.o_S + 6 * d + 3);
     w[M.o_QDB + d] += dot(sw, ubw + vw) + dot(sv, ubv + vv);
-    const V3 sbw = wd * Fn + qdd * an + qd * (ubw + vw);
-    const V3 sbv = wd * Ff + qdd * af + qd * (ubv + vv);
-    const int k = d - d0;
-    if (jt == J_FREE) {
-      if (k < 3) {
-        const V3 r = col(R, k);
-        const V3 rb = sbw + cross(sbv, P);
-        Pb = Pb + cross(r, sbv);
-        Rb.m[k] += rb.x; Rb.m[3 + k] += rb.y; Rb.m[6 + k] += rb.z;
-      } else {
-        Rb.m[k - 3] += sbv.x; Rb.m[3 + k - 3] += sbv.y; Rb.m[6 + k - 3] += sbv.z;
-      }
-    } else {
-      V3 ab;
-      if (jt == J_REV) {
-        const V3 a = mul(R, ax);
-        ab = sbw + cross(sbv, P);
-        Pb = Pb + cross(a, sbv);
-      } else {
-        ab = sbv;
-      }
-      add_outer(Rb, ab, ax);
+    sbw = wd * Fn + qdd * an + qd * (ubw + vw);
+    sbv = wd * Ff + qdd * af + qd * (ubv + vv);
+  };
+  if (jt == J_FREE) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {   // (R e_k, P x R e_k)
+      V3 sbw, sbv;
+      dof_terms(k, sbw, sbv);
+      const V3 rb = sbw + cross(sbv, P);
+      Pb = Pb + cross(col(R, k), sbv);
+      Rb.m[k] += rb.x; Rb.m[3 + k] += rb.y; Rb.m[6 + k] += rb.z;
     }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {   // (0, R e_k)
+      V3 sbw, sbv;
+      dof_terms(3 + k, sbw, sbv);
+      Rb.m[k] += sbv.x; Rb.m[3 + k] += sbv.y; Rb.m[6 + k] += sbv.z;
+    }
+  } else if (nd == 1) {
+    V3 sbw, sbv;
+    dof_terms(0, sbw, sbv);
+    V3 ab;
+    if (jt == J_REV) {   // (a, P x a), a = R ax
+      const V3 a = mul(R, ax);
+      ab = sbw + cross(sbv, P);
+      Pb = Pb + cross(a, sbv);
+    } else {             // (0, a)
+      ab = sbv;
+    }
+    add_outer(Rb, ab, ax);
   }
   stm(w, M.o_RB + 9 * i, Rb);
   st3(w, M.o_PB + 3 * i, Pb);

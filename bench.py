@@ -296,6 +296,29 @@ def gpu_main(args, rank, world, dist):
     ms_fwd = timed(one_fwd, max(3, args.steps // 2), 1)
     ms_adj = timed(one_adj, max(3, args.steps // 2), 1)
 
+    # ---- episodic window (early termination with in-kernel reset, gradient
+    # cut at resets), graph captured like the main window: the task heights and
+    # horizons of the models, seeded reset states, episode counters spread over
+    # the horizon
+    rules = [I.episode_rule(m) for m, _ in groups]
+    qr = sim.pack([I.initial_state(m, n, seed + 1)[0] for m, n in groups], "q")
+    qdr = sim.pack([I.initial_state(m, n, seed + 1)[1] for m, n in groups], "qd")
+    ep0 = np.concatenate([np.random.default_rng(seed).integers(0, hz, n) for (m, n), (_, hz) in zip(groups, rules)])
+    ep_step = torch.from_numpy(ep0.astype(np.int32)).to(dev)
+    th, hz = [r[0] for r in rules], [r[1] for r in rules]
+    with torch.cuda.stream(stream):
+        oef = sim.window_forward_episodic(q0, qd0, act, qr, qdr, th, hz, ep_step, stream=stream)
+        oea = sim.window_adjoint_episodic(oef[0], oef[1], act, oef[3], rbar, zq, zqd, stream=stream)
+    stream.synchronize()
+    graph_ep = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(stream):
+        with torch.cuda.graph(graph_ep, stream=stream):
+            sim.window_forward_episodic(q0, qd0, act, qr, qdr, th, hz, ep_step, out=oef, stream=stream)
+            sim.window_adjoint_episodic(oef[0], oef[1], act, oef[3], rbar, zq, zqd, out=oea, stream=stream)
+    stream.synchronize()
+    ms_episodic = timed(graph_ep.replay, args.steps, args.warmup)
+    done_frac = float(oef[3].float().mean())
+
     # gradient validity gate: sampled environments against the FP64 oracle
     grad_rel = None
     if rank == 0 and args.grad_check_envs > 0:
@@ -339,8 +362,8 @@ def gpu_main(args, rank, world, dist):
     d2h = 4 * (hrew.numel() + hab.numel() + hq0b.numel() + hqd0b.numel())
 
     # max over ranks
-    ms_batched, ms_plain, ms_e2e, ms_fwd, ms_adj = max_over_ranks([ms_batched, ms_plain, ms_e2e, ms_fwd, ms_adj],
-                                                                  dist, dev)
+    ms_batched, ms_plain, ms_e2e, ms_fwd, ms_adj, ms_episodic = max_over_ranks(
+        [ms_batched, ms_plain, ms_e2e, ms_fwd, ms_adj, ms_episodic], dist, dev)
     if rank != 0:
         return
     env_steps = n_envs * H * world
@@ -363,6 +386,10 @@ def gpu_main(args, rank, world, dist):
         "plain_form": {"value": plain_value, "unit": "env-steps/s", "ms_per_step": ms_plain,
                        "steps": args.plain_steps},
         "speedup_vs_plain": value / plain_value,
+        "episodic": {"value": env_steps / (ms_episodic * 1e-3), "unit": "env-steps/s", "ms_per_step": ms_episodic,
+                     "done_frac": done_frac,
+                     "rule": "root below the task height or the task horizon; seeded reset states; "
+                             "forward + adjoint with the gradient cut at resets, one CUDA graph"},
         "kernels_ms": {"k_batched_forward": ms_fwd, "k_batched_adjoint": ms_adj},
         "grad_rel_err_max": grad_rel,
         "gpu_launches": 2 * args.steps,

@@ -187,6 +187,49 @@ shac_status shac_window_adjoint(shac_batch* batch, void* stream, void* workspace
                                 const float* reward_bar, const float* q_traj_bar, const float* qd_traj_bar,
                                 float* q0_bar, float* qd0_bar, float* act_bar);
 
+/* Episodic window: early termination with an in-kernel reset and the gradient
+ * cut at the reset (Sec. 3.2: the environment is reset when the task terminates
+ * early and no gradient crosses the reset; appendix A.3: a task terminates when
+ * the root falls below a task height, or at the task horizon).  BATCHED form
+ * only (SHAC_ERR_UNSUPPORTED for PLAIN).
+ *
+ * shac_window_forward_episodic does what shac_window_forward does and, after
+ * every step t, for every environment:
+ *   e <- e + 1   (e = steps since the environment's last reset)
+ *   done_t = (the group's model has a free root and q[2], the root height,
+ *             < term_height[g])  or  (max_episode_steps[g] > 0 and e >= max_episode_steps[g])
+ *   if done_t: state <- the environment's reset state, e <- 0.
+ * reward[t] is the reward of step t before any reset; q_traj/qd_traj[t + 1]
+ * hold the state after the reset (the state step t + 1 starts from).
+ *   q_reset, qd_reset  reset states, same layout as q0/qd0 (device, read only).
+ *   term_height        HOST array [n_groups], copied; -INFINITY or NaN: no
+ *                      height rule for that group.
+ *   max_episode_steps  HOST array [n_groups], copied: task horizon per group
+ *                      in control steps; <= 0: none.
+ *   episode_step       device int32 [n_envs] (groups concatenated): e, read at
+ *                      the start of the window and written at its end.
+ *   done               device uint8 [h][n_envs]: 1 where step t ended an
+ *                      episode, else 0.
+ * The discount restart at a reset (Sec. 3.2) belongs to the caller's loss: it
+ * weights reward_bar with the done mask.
+ *
+ * shac_window_adjoint_episodic does what shac_window_adjoint does with the
+ * done mask of the forward window: where done_t, the cotangent of the state
+ * after step t (a reset state, a constant of the window), including
+ * q_traj_bar[t + 1], is dropped before step t is reversed; step t's reward
+ * cotangent still enters. */
+shac_status shac_window_forward_episodic(shac_batch* batch, void* stream, void* workspace, int32_t h,
+                                         const float* q0, const float* qd0, const float* act,
+                                         const float* q_reset, const float* qd_reset,
+                                         const float* term_height, const int32_t* max_episode_steps,
+                                         int32_t* episode_step, float* q_traj, float* qd_traj, float* reward,
+                                         uint8_t* done);
+shac_status shac_window_adjoint_episodic(shac_batch* batch, void* stream, void* workspace, int32_t h,
+                                         const float* q_traj, const float* qd_traj, const float* act,
+                                         const uint8_t* done, const float* reward_bar,
+                                         const float* q_traj_bar, const float* qd_traj_bar,
+                                         float* q0_bar, float* qd0_bar, float* act_bar);
+
 /* Step adjoint for callers that cannot allocate device memory when they call
  * the simulator (e.g. inside a CUDA graph capture that forbids allocation, or
  * runtimes that only pass pre-registered buffers).  The paper has no

@@ -196,6 +196,64 @@ class Oracle:
                                  qb.ctypes.data_as(_f64p), qdb.ctypes.data_as(_f64p), ab.ctypes.data_as(_f64p))
         return qb, qdb, ab
 
+    # ---- episodic window ---------------------------------------------------
+    # Sec. 3.2: the environment is reset when its task terminates early, and the
+    # gradient is cut at the reset.  Appendix A.3: a task terminates when the
+    # root falls below a task height, or at the task horizon.  Written plainly
+    # on top of step / step_vjp: one step at a time, the decision and the reset
+    # taken in float64 on the oracle's own state.
+    def window_forward_episodic(self, q0, qd0, act, q_reset, qd_reset, term_height, max_episode_steps, ep0):
+        """q0 [N,nq], qd0 [N,nv], act [h,N,na], q_reset/qd_reset like q0/qd0,
+        ep0 [N] steps since each environment's last reset.  After step t:
+        e += 1; done = (free root and q[2] < term_height) or
+        (max_episode_steps > 0 and e >= max_episode_steps); a done environment
+        restarts from its reset state with e = 0.
+        -> q_traj [h+1,N,nq] (states after any reset), qd_traj, rew [h,N] (rewards
+        before the reset), done [h,N] (uint8), e [N], and the states before the
+        reset q_pre [h,N,nq], qd_pre."""
+        act = np.asarray(act, np.float64)
+        h, N = act.shape[0], act.shape[1]
+        root_free = int(self.model.joint_type[0]) == 0
+        q = np.array(q0, np.float64); qd = np.array(qd0, np.float64)
+        qr = np.asarray(q_reset, np.float64); qdr = np.asarray(qd_reset, np.float64)
+        e = np.array(ep0, np.int64)
+        qt = [q.copy()]; qdt = [qd.copy()]; rw = np.zeros((h, N)); done = np.zeros((h, N), np.uint8)
+        q_pre = np.zeros((h, N, self.nq)); qd_pre = np.zeros((h, N, self.nv))
+        for t in range(h):
+            q, qd, rw[t] = self.step(q, qd, act[t])
+            q_pre[t], qd_pre[t] = q, qd
+            e = e + 1
+            d = np.zeros(N, bool)
+            if root_free:
+                d |= q[:, 2] < term_height
+            if max_episode_steps > 0:
+                d |= e >= max_episode_steps
+            done[t] = d
+            e[d] = 0
+            q = np.where(d[:, None], qr, q)
+            qd = np.where(d[:, None], qdr, qd)
+            qt.append(q.copy()); qdt.append(qd.copy())
+        return np.stack(qt), np.stack(qdt), rw, done, e, q_pre, qd_pre
+
+    def window_adjoint_episodic(self, q_traj, qd_traj, act, done, r_bar, q_traj_bar, qd_traj_bar):
+        """Reverse of the episodic window over its checkpoints (q_traj [h+1,N,nq]
+        after resets) and done mask: where done[t] the cotangent of the state
+        after step t is dropped (a reset state is a constant), then step t is
+        reversed with its reward cotangent r_bar[t].  q_traj_bar [h+1,N,nq] are
+        the direct cotangents of the checkpoints.  -> q0_bar, qd0_bar, act_bar [h,N,na]."""
+        act = np.asarray(act, np.float64)
+        h, N = act.shape[0], act.shape[1]
+        qb = np.array(q_traj_bar[h], np.float64); qdb = np.array(qd_traj_bar[h], np.float64)
+        ab = np.zeros((h, N, self.na))
+        for t in range(h - 1, -1, -1):
+            cut = np.asarray(done[t]).astype(bool)
+            qb[cut] = 0.0
+            qdb[cut] = 0.0
+            sq, sqd, ab[t] = self.step_vjp(q_traj[t], qd_traj[t], act[t], qb, qdb, r_bar[t])
+            qb = sq + q_traj_bar[t]
+            qdb = sqd + qd_traj_bar[t]
+        return qb, qdb, ab
+
     # ---- single state ------------------------------------------------------
     def forward_accel(self, q, qd, a):
         out = np.zeros(self.nv)

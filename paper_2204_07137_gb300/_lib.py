@@ -25,8 +25,8 @@ FORM_PLAIN, FORM_BATCHED = 0, 1
 EXPORTED = [
     "shac_model_create", "shac_model_destroy", "shac_model_dims", "shac_batch_create", "shac_batch_destroy",
     "shac_batch_dims", "shac_batch_workspace_bytes", "shac_step", "shac_step_adjoint", "shac_window_forward",
-    "shac_window_adjoint", "shac_batch_set_launch", "shac_batch_get_launch", "shac_get_status",
-    "shac_status_string", "shac_step_adjoint_static",
+    "shac_window_adjoint", "shac_window_forward_episodic", "shac_window_adjoint_episodic", "shac_batch_set_launch",
+    "shac_batch_get_launch", "shac_get_status", "shac_status_string", "shac_step_adjoint_static",
 ]
 
 
@@ -91,6 +91,10 @@ def load(path: str = LIB_PATH):
     L.shac_window_forward.restype = ctypes.c_int
     L.shac_window_adjoint.argtypes = [_vp, _vp, _vp, ctypes.c_int32] + [_vp] * 9
     L.shac_window_adjoint.restype = ctypes.c_int
+    L.shac_window_forward_episodic.argtypes = [_vp, _vp, _vp, ctypes.c_int32] + [_vp] * 12
+    L.shac_window_forward_episodic.restype = ctypes.c_int
+    L.shac_window_adjoint_episodic.argtypes = [_vp, _vp, _vp, ctypes.c_int32] + [_vp] * 10
+    L.shac_window_adjoint_episodic.restype = ctypes.c_int
     L.shac_batch_set_launch.argtypes = [_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]
     L.shac_batch_set_launch.restype = ctypes.c_int
     L.shac_batch_get_launch.argtypes = [_vp, ctypes.c_int32, _i32p, _i32p]

@@ -520,18 +520,41 @@ static shac_status batched_launch(shac_batch* b, BatchedArgs& a, void* ws, cudaS
   return cuda_ok(cudaGetLastError());
 }
 
+// Episodic-window arguments (early termination with reset); batched form only.
+struct Episodic {
+  const float* q_reset = nullptr;
+  const float* qd_reset = nullptr;
+  const float* term_height = nullptr;   // host [n_groups]
+  const int32_t* max_ep = nullptr;      // host [n_groups]
+  int* ep_step = nullptr;
+  unsigned char* done = nullptr;
+  const unsigned char* done_in = nullptr;
+};
+
+static void set_episodic(const shac_batch* b, BatchedArgs& a, const Episodic* ep) {
+  if (!ep) return;
+  a.q_reset = ep->q_reset; a.qd_reset = ep->qd_reset;
+  for (int gi = 0; gi < (int)b->groups.size(); ++gi) {
+    a.term_h[gi] = ep->term_height ? ep->term_height[gi] : -INFINITY;
+    a.max_ep[gi] = ep->max_ep ? ep->max_ep[gi] : 0;
+  }
+  a.ep_step = ep->ep_step; a.done = ep->done; a.done_in = ep->done_in;
+}
+
 static shac_status run_forward(shac_batch* b, cudaStream_t s, void* ws, int h, const float* q0, const float* qd0,
                                const float* act, float* q_out, float* qd_out, float* reward, float* q_copy0,
-                               float* qd_copy0) {
+                               float* qd_copy0, const Episodic* ep = nullptr) {
   if (b->form == SHAC_FORM_BATCHED) {
     BatchedArgs a{};
     a.h = h;
     a.q_in = q0; a.qd_in = qd0; a.act = act;
     a.q_out = q_out; a.qd_out = qd_out; a.reward = reward;
     a.q_copy0 = q_copy0; a.qd_copy0 = qd_copy0;
+    set_episodic(b, a, ep);
     // per-group tape offsets are not used by the forward kernel
     return batched_launch(b, a, ws, s, false);
   }
+  if (ep) return SHAC_ERR_UNSUPPORTED;
   if (q_copy0) {
     if (cudaMemcpyAsync(q_copy0, q0, b->q_size * sizeof(float), cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
         cudaMemcpyAsync(qd_copy0, qd0, b->qd_size * sizeof(float), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
@@ -558,15 +581,17 @@ static shac_status run_forward(shac_batch* b, cudaStream_t s, void* ws, int h, c
 static shac_status run_adjoint(shac_batch* b, cudaStream_t s, void* ws, int h, const float* q_traj,
                                const float* qd_traj, const float* act, const float* reward_bar, const float* qtb,
                                const float* qdtb, const float* qT_bar, const float* qdT_bar, float* q0_bar,
-                               float* qd0_bar, float* act_bar) {
+                               float* qd0_bar, float* act_bar, const Episodic* ep = nullptr) {
   if (b->form == SHAC_FORM_BATCHED) {
     BatchedArgs a{};
     a.h = h;
     a.q_traj = q_traj; a.qd_traj = qd_traj; a.act = act; a.reward_bar = reward_bar;
     a.qT_bar = qT_bar; a.qdT_bar = qdT_bar; a.qtb = qtb; a.qdtb = qdtb;
     a.q0_bar = q0_bar; a.qd0_bar = qd0_bar; a.act_bar = act_bar;
+    set_episodic(b, a, ep);
     return batched_launch(b, a, ws, s, true);
   }
+  if (ep) return SHAC_ERR_UNSUPPORTED;
   for (int gi = 0; gi < (int)b->groups.size(); ++gi) {
     if (b->groups[gi].N == 0) continue;
     PlainGroup p = plain_group(b, gi, ws);
@@ -635,6 +660,39 @@ extern "C" shac_status shac_window_adjoint(shac_batch* b, void* stream, void* ws
   return run_adjoint(b, (cudaStream_t)stream, ws, h, q_traj, qd_traj, act, reward_bar, q_traj_bar, qd_traj_bar,
                      q_traj_bar + (size_t)h * b->q_size, qd_traj_bar + (size_t)h * b->qd_size, q0_bar, qd0_bar,
                      act_bar);
+}
+
+extern "C" shac_status shac_window_forward_episodic(shac_batch* b, void* stream, void* ws, int32_t h,
+                                                    const float* q0, const float* qd0, const float* act,
+                                                    const float* q_reset, const float* qd_reset,
+                                                    const float* term_height, const int32_t* max_episode_steps,
+                                                    int32_t* episode_step, float* q_traj, float* qd_traj,
+                                                    float* reward, uint8_t* done) {
+  if (!b || !aligned_ws(b, ws) || h < 1 || h > b->h_max || !q0 || !qd0 || !act || !q_reset || !qd_reset ||
+      !term_height || !max_episode_steps || !episode_step || !q_traj || !qd_traj || !reward || !done)
+    return SHAC_ERR_INVALID_ARG;
+  if (b->form != SHAC_FORM_BATCHED) return SHAC_ERR_UNSUPPORTED;
+  Episodic ep;
+  ep.q_reset = q_reset; ep.qd_reset = qd_reset; ep.term_height = term_height;
+  ep.max_ep = max_episode_steps; ep.ep_step = episode_step; ep.done = done;
+  return run_forward(b, (cudaStream_t)stream, ws, h, q0, qd0, act, q_traj + b->q_size, qd_traj + b->qd_size, reward,
+                     q_traj, qd_traj, &ep);
+}
+
+extern "C" shac_status shac_window_adjoint_episodic(shac_batch* b, void* stream, void* ws, int32_t h,
+                                                    const float* q_traj, const float* qd_traj, const float* act,
+                                                    const uint8_t* done, const float* reward_bar,
+                                                    const float* q_traj_bar, const float* qd_traj_bar,
+                                                    float* q0_bar, float* qd0_bar, float* act_bar) {
+  if (!b || !aligned_ws(b, ws) || h < 1 || h > b->h_max || !q_traj || !qd_traj || !act || !done || !reward_bar ||
+      !q_traj_bar || !qd_traj_bar || !q0_bar || !qd0_bar || !act_bar)
+    return SHAC_ERR_INVALID_ARG;
+  if (b->form != SHAC_FORM_BATCHED) return SHAC_ERR_UNSUPPORTED;
+  Episodic ep;
+  ep.done_in = done;
+  return run_adjoint(b, (cudaStream_t)stream, ws, h, q_traj, qd_traj, act, reward_bar, q_traj_bar, qd_traj_bar,
+                     q_traj_bar + (size_t)h * b->q_size, qd_traj_bar + (size_t)h * b->qd_size, q0_bar, qd0_bar,
+                     act_bar, &ep);
 }
 
 // ---------------------------------------------------------------------------

@@ -208,6 +208,8 @@ __device__ void forward_item(const BatchedArgs& a, const DevModel& M, const Work
     team_store(w, M.o_Q, a.q_copy0 + io.q_off, M.nq, io.N, t.env, t.lane, t.nl, t.active);
     team_store(w, M.o_QD, a.qd_copy0 + io.qd_off, M.nv, io.N, t.env, t.lane, t.nl, t.active);
   }
+  int ep = 0;   // episodic window: steps since the last reset (team lane 0)
+  if (a.done && t.lane == 0) ep = a.ep_step[io.env_off + t.env];
   for (int step = 0; step < a.h; ++step) {
     team_load(w, M.o_ACT, a.act + (size_t)step * a.io.act_size + io.act_off, M.na, io.N, t.env, t.lane, t.nl);
     clear_comp(M, w, t.lane, t.nl);
@@ -216,15 +218,32 @@ __device__ void forward_item(const BatchedArgs& a, const DevModel& M, const Work
       substep_dynamics(M, w, t.lane, t.nl, nm);
       st_integrate(M, w, t.lane, t.nl);
     }
-    team_store(w, M.o_Q, a.q_out + (size_t)step * a.io.q_size + io.q_off, M.nq, io.N, t.env, t.lane, t.nl, t.active);
-    team_store(w, M.o_QD, a.qd_out + (size_t)step * a.io.qd_size + io.qd_off, M.nv, io.N, t.env, t.lane, t.nl,
-               t.active);
     if (t.lane == 0 && t.active) {
       a.reward[(size_t)step * a.io.n_envs + io.env_off + t.env] = reward_value(M, w);
       if (!state_finite(M, w)) atomicOr(a.flags, FLAG_NONFINITE);
     }
+    if (a.done) {   // early termination (root below the task height, or the episode length) and reset
+      team_sync(t.nl);
+      int d = 0;
+      if (t.lane == 0) {
+        ++ep;
+        d = ((M.root_free && w[M.o_Q + 2] < a.term_h[it.group]) || (a.max_ep[it.group] > 0 && ep >= a.max_ep[it.group])) ? 1 : 0;
+        if (d) ep = 0;
+        if (t.active) a.done[(size_t)step * a.io.n_envs + io.env_off + t.env] = (unsigned char)d;
+      }
+      d = __shfl_sync(0xffffffffu, d, 0, t.nl);
+      if (d) {
+        team_load(w, M.o_Q, a.q_reset + io.q_off, M.nq, io.N, t.env, t.lane, t.nl);
+        team_load(w, M.o_QD, a.qd_reset + io.qd_off, M.nv, io.N, t.env, t.lane, t.nl);
+      }
+      team_sync(t.nl);
+    }
+    team_store(w, M.o_Q, a.q_out + (size_t)step * a.io.q_size + io.q_off, M.nq, io.N, t.env, t.lane, t.nl, t.active);
+    team_store(w, M.o_QD, a.qd_out + (size_t)step * a.io.qd_size + io.qd_off, M.nv, io.N, t.env, t.lane, t.nl,
+               t.active);
     team_sync(t.nl);
   }
+  if (a.done && t.lane == 0 && t.active) a.ep_step[io.env_off + t.env] = ep;
 }
 
 // Reload a substep record (global -> shared) with asynchronous copies, all in
@@ -256,6 +275,11 @@ __device__ void adjoint_item(const BatchedArgs& a, const DevModel& M, const Work
     team_load(w, M.o_QD, a.qd_traj + (size_t)step * a.io.qd_size + io.qd_off, M.nv, io.N, t.env, t.lane, t.nl);
     team_load(w, M.o_ACT, a.act + (size_t)step * a.io.act_size + io.act_off, M.na, io.N, t.env, t.lane, t.nl);
     zero_range(w, M.o_ACTB, M.na, t.lane, t.nl);
+    if (a.done_in && a.done_in[(size_t)step * a.io.n_envs + io.env_off + t.env]) {
+      // the state after this step was a reset state: no gradient crosses the reset
+      zero_range(w, M.o_QB, M.nq, t.lane, t.nl);
+      zero_range(w, M.o_QDB, M.nv, t.lane, t.nl);
+    }
     clear_comp(M, w, t.lane, t.nl);
     team_sync(t.nl);
     for (int k = 0; k < M.K; ++k) {

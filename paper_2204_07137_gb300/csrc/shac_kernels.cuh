@@ -59,6 +59,14 @@ struct BatchedArgs {
   float* q0_bar;
   float* qd0_bar;
   float* act_bar;           // [h][act_size]
+  // episodic window (early termination with reset); null / unused otherwise
+  const float* q_reset;     // reset states, layout of q_in
+  const float* qd_reset;
+  float term_h[MAX_GROUPS]; // root-height threshold per group (-inf / NaN: none)
+  int max_ep[MAX_GROUPS];   // episode length limit per group (<= 0: none)
+  int* ep_step;             // [n_envs] steps since the last reset (in/out)
+  unsigned char* done;      // forward: [h][n_envs] episode ended by step t
+  const unsigned char* done_in;   // adjoint: the forward's done mask
 };
 
 void launch_batched_forward(const BatchedArgs& a, int grid, int block, size_t smem, cudaStream_t s);

@@ -631,3 +631,15 @@ def workload(name: str, scale: float = 1.0) -> Workload:
 
 
 WORKLOADS = ["cartpole-64", "ant-2048", "humanoid-1024", "hetero-4096-2048-1024", "mtu-512"]
+
+# Episode rules of the tasks (appendix A.3): root height below which the task
+# terminates early (-inf: no early termination) and the task horizon in control
+# steps.  The root of the ant-like model is the torso, of the humanoid-like model
+# the torso, of the muscle model the pelvis.
+EPISODE_RULES = {"cartpole": (-np.inf, 240), "ant": (0.27, 1000), "humanoid": (0.74, 1000), "mtu": (0.46, 1000)}
+
+
+def episode_rule(model: ArticulationModel) -> Tuple[float, int]:
+    """(termination height, task horizon) of a model built by this module."""
+    return EPISODE_RULES[model.name]
+

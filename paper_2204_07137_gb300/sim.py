@@ -147,6 +147,62 @@ class Simulator:
                    "shac_window_adjoint")
         return out
 
+    def window_forward_episodic(self, q0, qd0, act, q_reset, qd_reset, term_height, max_episode_steps,
+                                episode_step, out=None, stream=None):
+        """Window with early termination and reset (see shacsim.h).
+        term_height, max_episode_steps: one value per group (-inf / 0: no such
+        rule); episode_step: int32 CUDA tensor [n_envs], updated in place.
+        -> (q_traj [h+1, q_size], qd_traj, reward [h, n_envs], done uint8 [h, n_envs])."""
+        h = int(act.shape[0])
+        if out is None:
+            out = (torch.empty(h + 1, self.q_size, device=self.device),
+                   torch.empty(h + 1, self.qd_size, device=self.device),
+                   torch.empty(h, self.n_envs, device=self.device),
+                   torch.empty(h, self.n_envs, dtype=torch.uint8, device=self.device))
+        if not (episode_step.is_cuda and episode_step.dtype == torch.int32 and episode_step.is_contiguous()
+                and episode_step.numel() == self.n_envs):
+            raise ValueError(f"episode_step: expected contiguous int32 CUDA tensor with {self.n_envs} elements")
+        d = out[3]
+        if not (d.is_cuda and d.dtype == torch.uint8 and d.is_contiguous() and d.numel() == h * self.n_envs):
+            raise ValueError(f"done: expected contiguous uint8 CUDA tensor with {h * self.n_envs} elements")
+        th, hz = list(term_height), list(max_episode_steps)
+        if len(th) != len(self.groups) or len(hz) != len(self.groups):
+            raise ValueError(f"term_height, max_episode_steps: expected {len(self.groups)} values (one per group)")
+        th_c = (ctypes.c_float * len(th))(*[float(x) for x in th])
+        hz_c = (ctypes.c_int32 * len(hz))(*[int(x) for x in hz])
+        args = [self._check(q0, self.q_size, "q0"), self._check(qd0, self.qd_size, "qd0"),
+                self._check(act, h * self.act_size, "act"), self._check(q_reset, self.q_size, "q_reset"),
+                self._check(qd_reset, self.qd_size, "qd_reset"), ctypes.cast(th_c, ctypes.c_void_p),
+                ctypes.cast(hz_c, ctypes.c_void_p), ctypes.c_void_p(episode_step.data_ptr()),
+                self._check(out[0], (h + 1) * self.q_size, "q_traj"),
+                self._check(out[1], (h + 1) * self.qd_size, "qd_traj"),
+                self._check(out[2], h * self.n_envs, "reward"), ctypes.c_void_p(d.data_ptr())]
+        _lib.check(_lib.load().shac_window_forward_episodic(self.batch, self._stream(stream), self._ws(), h, *args),
+                   "shac_window_forward_episodic")
+        return out
+
+    def window_adjoint_episodic(self, q_traj, qd_traj, act, done, reward_bar, q_traj_bar, qd_traj_bar, out=None,
+                                stream=None):
+        """Reverse of an episodic window: no gradient crosses a reset (done mask
+        of the forward) -> (q0_bar, qd0_bar, act_bar [h, act_size])."""
+        h = int(act.shape[0])
+        if out is None:
+            out = (torch.empty(self.q_size, device=self.device), torch.empty(self.qd_size, device=self.device),
+                   torch.empty(h, self.act_size, device=self.device))
+        if not (done.is_cuda and done.dtype == torch.uint8 and done.is_contiguous() and done.numel() == h * self.n_envs):
+            raise ValueError(f"done: expected contiguous uint8 CUDA tensor with {h * self.n_envs} elements")
+        args = [self._check(q_traj, (h + 1) * self.q_size, "q_traj"),
+                self._check(qd_traj, (h + 1) * self.qd_size, "qd_traj"),
+                self._check(act, h * self.act_size, "act"), ctypes.c_void_p(done.data_ptr()),
+                self._check(reward_bar, h * self.n_envs, "reward_bar"),
+                self._check(q_traj_bar, (h + 1) * self.q_size, "q_traj_bar"),
+                self._check(qd_traj_bar, (h + 1) * self.qd_size, "qd_traj_bar"),
+                self._check(out[0], self.q_size, "q0_bar"), self._check(out[1], self.qd_size, "qd0_bar"),
+                self._check(out[2], h * self.act_size, "act_bar")]
+        _lib.check(_lib.load().shac_window_adjoint_episodic(self.batch, self._stream(stream), self._ws(), h, *args),
+                   "shac_window_adjoint_episodic")
+        return out
+
     def status(self, clear: bool = False, stream=None) -> int:
         """Sticky device flags (bit 0: a non-finite state was produced). Synchronises."""
         v = ctypes.c_uint32()
@@ -173,6 +229,18 @@ class Simulator:
             out.append(x[..., off:off + d * n].reshape(x.shape[:-1] + (d, n)))
             off += d * n
         return out
+
+
+def episode_discounts(done: torch.Tensor, gamma: float) -> torch.Tensor:
+    """Reward weights gamma^(t - t0) of the policy loss (Eq. policy_loss) with the
+    discount restarted after every reset (Sec. 3.2): done [h, N] (uint8, from
+    window_forward_episodic) -> [h, N] float32 whose row 0 is all ones and
+    whose row t + 1 is 1 where step t ended an episode, else gamma x row t."""
+    h = int(done.shape[0])
+    w = torch.ones(tuple(done.shape), dtype=torch.float32, device=done.device)
+    for t in range(1, h):
+        w[t] = torch.where(done[t - 1].bool(), torch.ones_like(w[t]), w[t - 1] * gamma)
+    return w
 
 
 # ------------------------------------------------------------ autograd --

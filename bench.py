@@ -56,11 +56,11 @@ ALGO_FLOPS_PER_ENV_STEP = {
     "ant-2048": {"forward": 137284, "adjoint": 137148 + 183668},
 }
 
-# DRAM traffic (read + write) per launch of each batched kernel at h = 32,
-# scaled from an ncu capture at h = 2 by the 16x env-steps (the per-step
-# traffic is the same at every step).  Empty until the counters are taken
-# again on the current kernels (roofline.traffic is then null).
-TRAFFIC_BYTES_PER_LAUNCH = {}
+# DRAM traffic (read + write) per launch of each batched kernel at h = 32 on
+# ant-2048, scaled from an ncu capture at h = 2 by the 16x env-steps (the
+# per-step traffic is the same at every step); profiles/batched_ant_2048.md.
+TRAFFIC_BYTES_PER_LAUNCH = {"ant-2048": {"k_batched_forward": 16 * (0.477696e6 + 0.0),
+                                         "k_batched_adjoint": 16 * (6.149632e6 + 105.850368e6)}}
 
 # Algorithmic HBM bytes per env-step (ant): forward reads the action (8 f32)
 # and writes the checkpoint (29) and reward (1); the adjoint reads checkpoint

@@ -53,7 +53,7 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # recomputes a step's substeps once, so its count is one forward recompute
 # plus the reverse-only stages.  Workloads without a count report achieved=null.
 ALGO_FLOPS_PER_ENV_STEP = {
-    "ant-2048": {"forward": 137284, "adjoint": 137148 + 183668},
+    "ant-2048": {"forward": 134692, "adjoint": 134556 + 172338},
 }
 
 # DRAM traffic (read + write) per launch of each batched kernel at h = 32 on
@@ -79,6 +79,11 @@ def parse():
     p.add_argument("--workload", default=WORKLOAD)
     p.add_argument("--grad-check-envs", type=int, default=4,
                    help="sampled environments of the first group checked against the oracle (0: skip)")
+    p.add_argument("--h-sweep", default="",
+                   help="window-length study instead of the contract line: comma-separated h values; "
+                        "N = samples // h environments of the workload's first model (see --samples)")
+    p.add_argument("--samples", type=int, default=65536,
+                   help="env-steps per window of the --h-sweep study (N x h)")
     return p.parse_args()
 
 
@@ -214,6 +219,68 @@ def max_over_ranks(values, dist, device=None):
     t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return t.tolist()
+
+
+# -------------------------------------------------------- h-sweep study ---
+def h_sweep_main(args):
+    """Window-length study (the paper's horizon study: every variant draws
+    the same number of samples per learning episode, N x h fixed): for each
+    h, N = samples // h environments run the graph-captured forward + adjoint
+    window; one JSON line with env-steps/s, ms per window and the kernel split
+    per h.  L2 flushed before each timed window."""
+    import torch
+    from paper_2204_07137_gb300 import build, inputs as I
+    from paper_2204_07137_gb300.sim import Simulator
+
+    build.build()
+    dev = torch.device("cuda", 0)
+    model = I.workload(args.workload).groups[0][0]
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    rows = []
+    for h in [int(x) for x in args.h_sweep.split(",")]:
+        N = max(1, args.samples // h)
+        sim = Simulator([(model, N)], form="batched", h_max=h)
+        q0, qd0 = (torch.from_numpy(np.ascontiguousarray(x.reshape(-1))).to(dev) for x in I.initial_state(model, N, 0))
+        act = torch.from_numpy(I.window_actions(model, N, h, 0).reshape(h, -1)).to(dev).contiguous()
+        rbar = torch.full((h, N), 1.0 / (N * h), device=dev)
+        zq = torch.zeros(h + 1, sim.q_size, device=dev)
+        zqd = torch.zeros(h + 1, sim.qd_size, device=dev)
+        with torch.cuda.stream(stream):
+            f = sim.window_forward(q0, qd0, act, stream=stream)
+            a = sim.window_adjoint(f[0], f[1], act, rbar, zq, zqd, stream=stream)
+        stream.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(stream):
+            with torch.cuda.graph(graph, stream=stream):
+                sim.window_forward(q0, qd0, act, out=f, stream=stream)
+                sim.window_adjoint(f[0], f[1], act, rbar, zq, zqd, out=a, stream=stream)
+        stream.synchronize()
+        times = {}
+        with torch.cuda.stream(stream):
+            for name, fn in (("window", graph.replay),
+                             ("forward", lambda: sim.window_forward(q0, qd0, act, out=f, stream=stream)),
+                             ("adjoint", lambda: sim.window_adjoint(f[0], f[1], act, rbar, zq, zqd, out=a,
+                                                                    stream=stream))):
+                for _ in range(args.warmup):
+                    fn()
+                total = 0.0
+                for _ in range(args.steps):
+                    flush.zero_()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    fn()
+                    e1.record(stream)
+                    e1.synchronize()
+                    total += e0.elapsed_time(e1)
+                times[name] = total / args.steps
+        assert sim.status() == 0 and torch.isfinite(a[2]).all()
+        rows.append({"h": h, "n_envs": N, "env_steps_per_s": N * h / (times["window"] * 1e-3),
+                     "ms_per_window": times["window"], "ms_forward": times["forward"], "ms_adjoint": times["adjoint"],
+                     "lanes_per_env": sim.get_launch(0)[0]})
+        del sim
+    print(json.dumps({"study": "window length h, N x h fixed", "model": model.name, "samples": args.samples,
+                      "dtype": "f32", "data": "synthetic", "rows": rows}), flush=True)
 
 
 # ------------------------------------------------------------------- GPU ---
@@ -450,6 +517,9 @@ def main():
     try:
         if args.impl == "reference":
             reference_main(args, rank, world)
+        elif args.h_sweep:
+            if rank == 0:
+                h_sweep_main(args)
         else:
             gpu_main(args, rank, world, dist)
     finally:

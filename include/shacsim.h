@@ -92,9 +92,15 @@ typedef struct shac_batch shac_batch;
  *                   action held; gravity[3].
  *  ke, kd, kt, mu:  contact normal stiffness, damping, friction stiffness, friction coefficient.
  *  rw_q[nq], rw_qd[nv], reward_coef[10]: reward on the post-step state,
- *     r = -sum rw_q q^2 - sum rw_qd qd^2 - c0 |a|^2
- *         + (free root only) c1 vx + c2 up_z + c3 head_x + Rh(clip(z - c4, c5, c6)),
- *     Rh(D) = c7 D^2 + c8 D (D < 0), c9 D (D >= 0).
+ *     r = -sum rw_q q^2 - sum rw_qd qd^2 - c0 |a|^2 + c1 vx + Rh(clip(z - c4, c5, c6))
+ *         + (free root only) c2 up_z + c3 head_x,
+ *     Rh(D) = c7 D^2 + c8 D (D < 0), c9 D (D >= 0).  With a free root, vx is
+ *     the world x velocity of the root origin and z = q[2] its height; without
+ *     one, vx = qd[vx_dof] and z = q[height_q] (a term whose index is -1 is
+ *     dropped: planar models driven through slide joints along x and z).
+ *  height_q, vx_dof: see the reward; height_q is also the root height of the
+ *     episodic window's termination rule for models without a free root.
+ *     Ignored for a free root.
  */
 typedef struct {
   int32_t n_links;
@@ -130,6 +136,8 @@ typedef struct {
   const float* rw_q;
   const float* rw_qd;
   float reward_coef[10];
+  int32_t height_q;
+  int32_t vx_dof;
 } shac_model_desc;
 
 /* Validate and copy a model description.  Returns SHAC_ERR_MODEL for a
@@ -196,8 +204,8 @@ shac_status shac_window_adjoint(shac_batch* batch, void* stream, void* workspace
  * shac_window_forward_episodic does what shac_window_forward does and, after
  * every step t, for every environment:
  *   e <- e + 1   (e = steps since the environment's last reset)
- *   done_t = (the group's model has a free root and q[2], the root height,
- *             < term_height[g])  or  (max_episode_steps[g] > 0 and e >= max_episode_steps[g])
+ *   done_t = (root height < term_height[g]: q[2] for a free root, else
+ *             q[height_q] when height_q >= 0)  or  (max_episode_steps[g] > 0 and e >= max_episode_steps[g])
  *   if done_t: state <- the environment's reset state, e <- 0.
  * reward[t] is the reward of step t before any reset; q_traj/qd_traj[t + 1]
  * hold the state after the reset (the state step t + 1 starts from).

@@ -43,6 +43,7 @@ class OrcDesc(ctypes.Structure):
         ("dt", ctypes.c_double), ("substeps", ctypes.c_int32), ("gravity", ctypes.c_double * 3),
         ("ke", ctypes.c_double), ("kd", ctypes.c_double), ("kt", ctypes.c_double), ("mu", ctypes.c_double),
         ("rw_q", _f64p), ("rw_qd", _f64p), ("reward_coef", ctypes.c_double * 10),
+        ("height_q", ctypes.c_int32), ("vx_dof", ctypes.c_int32),
     ]
 
 
@@ -152,6 +153,8 @@ class Oracle:
         desc.rw_qd = d(m.rw_qd)
         for k in range(10):
             desc.reward_coef[k] = float(m.reward_coef[k])
+        desc.height_q = int(m.height_q)
+        desc.vx_dof = int(m.vx_dof)
         self._keep = keep
         self.desc = desc
         self.nq, self.nv, self.na = m.nq, m.nv, m.na
@@ -205,7 +208,8 @@ class Oracle:
     def window_forward_episodic(self, q0, qd0, act, q_reset, qd_reset, term_height, max_episode_steps, ep0):
         """q0 [N,nq], qd0 [N,nv], act [h,N,na], q_reset/qd_reset like q0/qd0,
         ep0 [N] steps since each environment's last reset.  After step t:
-        e += 1; done = (free root and q[2] < term_height) or
+        e += 1; done = (root height < term_height: q[2] for a free root, else
+        q[height_q] when height_q >= 0) or
         (max_episode_steps > 0 and e >= max_episode_steps); a done environment
         restarts from its reset state with e = 0.
         -> q_traj [h+1,N,nq] (states after any reset), qd_traj, rew [h,N] (rewards
@@ -213,7 +217,7 @@ class Oracle:
         reset q_pre [h,N,nq], qd_pre."""
         act = np.asarray(act, np.float64)
         h, N = act.shape[0], act.shape[1]
-        root_free = int(self.model.joint_type[0]) == 0
+        hq = 2 if int(self.model.joint_type[0]) == 0 else int(self.model.height_q)   # root height coordinate
         q = np.array(q0, np.float64); qd = np.array(qd0, np.float64)
         qr = np.asarray(q_reset, np.float64); qdr = np.asarray(qd_reset, np.float64)
         e = np.array(ep0, np.int64)
@@ -224,8 +228,8 @@ class Oracle:
             q_pre[t], qd_pre[t] = q, qd
             e = e + 1
             d = np.zeros(N, bool)
-            if root_free:
-                d |= q[:, 2] < term_height
+            if hq >= 0:
+                d |= q[:, hq] < term_height
             if max_episode_steps > 0:
                 d |= e >= max_episode_steps
             done[t] = d

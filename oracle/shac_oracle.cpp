@@ -88,6 +88,7 @@ struct Model {
   std::vector<int> mptr, vlink; std::vector<double> vpos, fmax;
   double dt = 0; int K = 1; double g[3] = {0, 0, 0}; double ke = 0, kd = 0, kt = 0, mu = 0;
   std::vector<double> rwq, rwqd; double rc[10] = {0};
+  int height_q = -1, vx_dof = -1;   // reward coordinates of a model without a free root
 };
 
 template <class T> using V3 = std::array<T, 3>;
@@ -493,11 +494,21 @@ T reward(const Model& m, const T* q, const T* qd, const T* act) {
   T a2 = T(0.0);
   for (int j = 0; j < m.na; ++j) a2 = a2 + act[j] * act[j];
   r = r - m.rc[0] * a2;
+  // forward velocity, uprightness and heading, height: with a free root its
+  // world x velocity, R[2][2], R[0][0] and q[2]; without one (planar models on
+  // slide joints) qd[vx_dof] and q[height_q] when given
+  int hq = -1;
   if (m.L > 0 && m.jtype[0] == J_FREE) {
     M3<T> R = quat_rot(q[3], q[4], q[5], q[6]);
     V3<T> vw = mv(R, V3<T>{qd[3], qd[4], qd[5]});
     r = r + m.rc[1] * vw[0] + m.rc[2] * R[8] + m.rc[3] * R[0];
-    T D = q[2] - m.rc[4];
+    hq = 2;
+  } else {
+    if (m.vx_dof >= 0) r = r + m.rc[1] * qd[m.vx_dof];
+    hq = m.height_q;
+  }
+  if (hq >= 0) {
+    T D = q[hq] - m.rc[4];
     if (val(D) < m.rc[5]) D = T(m.rc[5]);
     if (val(D) > m.rc[6]) D = T(m.rc[6]);
     if (val(D) < 0.0) r = r + m.rc[7] * D * D + m.rc[8] * D;
@@ -574,6 +585,7 @@ typedef struct {
   int32_t n_muscles; const int32_t* muscle_ptr; const int32_t* via_link; const double* via_pos; const double* muscle_fmax;
   double dt; int32_t substeps; double gravity[3]; double ke, kd, kt, mu;
   const double* rw_q; const double* rw_qd; double reward_coef[10];
+  int32_t height_q; int32_t vx_dof;
 } orc_desc;
 
 static orc::Model make_model(const orc_desc* d) {
@@ -629,6 +641,8 @@ static orc::Model make_model(const orc_desc* d) {
   m.rwq.assign(d->rw_q, d->rw_q + nq);
   m.rwqd.assign(d->rw_qd, d->rw_qd + nv);
   for (int a = 0; a < 10; ++a) m.rc[a] = d->reward_coef[a];
+  m.height_q = d->height_q;
+  m.vx_dof = d->vx_dof;
   return m;
 }
 

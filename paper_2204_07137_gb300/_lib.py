@@ -45,6 +45,7 @@ class ShacModelDesc(ctypes.Structure):
         ("dt", ctypes.c_float), ("substeps", ctypes.c_int32), ("gravity", ctypes.c_float * 3),
         ("ke", ctypes.c_float), ("kd", ctypes.c_float), ("kt", ctypes.c_float), ("mu", ctypes.c_float),
         ("rw_q", _f32p), ("rw_qd", _f32p), ("reward_coef", ctypes.c_float * 10),
+        ("height_q", ctypes.c_int32), ("vx_dof", ctypes.c_int32),
     ]
 
 
@@ -162,6 +163,8 @@ class ModelHandle:
         d.rw_q, d.rw_qd = f(m.rw_q), f(m.rw_qd)
         for k in range(10):
             d.reward_coef[k] = float(m.reward_coef[k])
+        d.height_q = int(m.height_q)
+        d.vx_dof = int(m.vx_dof)
         h = _vp()
         check(L.shac_model_create(ctypes.byref(d), ctypes.byref(h)), "shac_model_create")
         self.handle = h

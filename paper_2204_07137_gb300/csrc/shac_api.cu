@@ -15,6 +15,7 @@ struct shac_model {
   int L = 0, nq = 0, nv = 0, na = 0, ntact = 0, nc = 0, nm = 0, nseg = 0, nitems = 0, K = 1, nlev = 0;
   float h = 0, grav[3] = {0, 0, 0}, ke = 0, kd = 0, kt = 0, mu = 0, klim = 0, rc[10] = {0};
   int root_free = 0;
+  int height_q = -1, vx_dof = -1;   // reward / termination coordinates (free root: 2 / world vx)
   std::vector<int> parent, jtype, qs, ds, nd, lvl_ptr, lvl_link, ch_ptr, ch_idx, li_ptr, li_idx, dof_link, dof_k,
       dof_act, item_link, seg_mus, mus_seg_ptr, anc_mask, chain_tail;
   std::vector<float> axis, jpos, jrot, mass, com, icom, qlo, qhi, arm, damp, gear, item_pos, crad, fmax, rwq, rwqd;
@@ -69,6 +70,8 @@ static void compute_layout(shac_model* m) {
   d.ke = m->ke; d.kd = m->kd; d.kt = m->kt; d.mu = m->mu; d.klim = m->klim;
   for (int k = 0; k < 10; ++k) d.rc[k] = m->rc[k];
   d.root_free = m->root_free;
+  d.height_q = m->height_q;
+  d.vx_dof = m->vx_dof;
   const int L = m->L, nv = m->nv, ni = m->nitems;
   int o = 0;
   auto take = [&](int& off, int n) { off = o; o += n; };
@@ -116,6 +119,16 @@ extern "C" shac_status shac_model_create(const shac_model_desc* dsc, shac_model*
   if (nv > MAX_DOF) { delete m; return SHAC_ERR_CAPACITY; }
   m->nq = nq; m->nv = nv;
   m->root_free = m->jtype[0] == J_FREE;
+  if (m->root_free) {
+    m->height_q = 2;   // root origin height; the forward velocity is the root's world vx
+  } else {
+    if (dsc->height_q < -1 || dsc->height_q >= nq || dsc->vx_dof < -1 || dsc->vx_dof >= nv) {
+      delete m;
+      return SHAC_ERR_MODEL;
+    }
+    m->height_q = dsc->height_q;
+    m->vx_dof = dsc->vx_dof;
+  }
   for (int i = 0; i < L; ++i) {
     float a[3] = {dsc->joint_axis[3 * i], dsc->joint_axis[3 * i + 1], dsc->joint_axis[3 * i + 2]};
     float n = std::sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);

@@ -53,6 +53,7 @@ struct DevModel {
   float grav[3], ke, kd, kt, mu, klim;
   float rc[10];
   int root_free;                         // link 0 is a free joint
+  int height_q, vx_dof;                  // root height / forward velocity coordinates (q[2] / world vx with a free root)
   // links
   const int *parent, *jtype, *qs, *ds, *nd;
   const int *lvl_ptr, *lvl_link;         // chain heads grouped by chain depth
@@ -887,7 +888,11 @@ __device__ float reward_value(const DevModel& M, const Mem& w) {
     M33 R = quat_to_R(w[M.o_Q + 3], w[M.o_Q + 4], w[M.o_Q + 5], w[M.o_Q + 6]);
     V3 vw = mul(R, ld3(w, M.o_QD + 3));
     r += M.rc[1] * vw.x + M.rc[2] * R.m[8] + M.rc[3] * R.m[0];
-    float D = fminf(fmaxf(w[M.o_Q + 2] - M.rc[4], M.rc[5]), M.rc[6]);
+  } else if (M.vx_dof >= 0) {
+    r += M.rc[1] * w[M.o_QD + M.vx_dof];
+  }
+  if (M.height_q >= 0) {
+    float D = fminf(fmaxf(w[M.o_Q + M.height_q] - M.rc[4], M.rc[5]), M.rc[6]);
     r += D < 0.f ? (M.rc[7] * D * D + M.rc[8] * D) : M.rc[9] * D;
   }
   return r;
@@ -914,11 +919,14 @@ __device__ void reward_adjoint(const DevModel& M, const Mem& w, float rb) {
     float xb = 0.f, yb = 0.f, zb = 0.f, wb = 0.f;
     quat_to_R_adj(x, y, z, qw, B, xb, yb, zb, wb);
     w[M.o_QB + 3] += xb; w[M.o_QB + 4] += yb; w[M.o_QB + 5] += zb; w[M.o_QB + 6] += wb;
-    float raw = w[M.o_Q + 2] - M.rc[4];
+  } else if (M.vx_dof >= 0) {
+    w[M.o_QDB + M.vx_dof] += M.rc[1] * rb;
+  }
+  if (M.height_q >= 0) {
+    const float raw = w[M.o_Q + M.height_q] - M.rc[4];
     if (raw > M.rc[5] && raw < M.rc[6]) {
-      float D = raw;
-      float dD = D < 0.f ? (2.f * M.rc[7] * D + M.rc[8]) : M.rc[9];
-      w[M.o_QB + 2] += dD * rb;
+      const float dD = raw < 0.f ? (2.f * M.rc[7] * raw + M.rc[8]) : M.rc[9];
+      w[M.o_QB + M.height_q] += dD * rb;
     }
   }
 }

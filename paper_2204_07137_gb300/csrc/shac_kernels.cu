@@ -227,7 +227,7 @@ __device__ void forward_item(const BatchedArgs& a, const DevModel& M, const Work
       int d = 0;
       if (t.lane == 0) {
         ++ep;
-        d = ((M.root_free && w[M.o_Q + 2] < a.term_h[it.group]) || (a.max_ep[it.group] > 0 && ep >= a.max_ep[it.group])) ? 1 : 0;
+        d = ((M.height_q >= 0 && w[M.o_Q + M.height_q] < a.term_h[it.group]) || (a.max_ep[it.group] > 0 && ep >= a.max_ep[it.group])) ? 1 : 0;
         if (d) ep = 0;
         if (t.active) a.done[(size_t)step * a.io.n_envs + io.env_off + t.env] = (unsigned char)d;
       }

@@ -48,12 +48,14 @@ class ArticulationModel:
 
     Reward (evaluated on the post-step state with the step's action):
       r = - sum_j rw_q[j] q_j^2 - sum_j rw_qd[j] qd_j^2 - w_act * |a|^2
-          + [free root only] w_v * vx + w_up * up_z + w_head * head_x + R_h
+          + w_v * vx + R_h + [free root only] w_up * up_z + w_head * head_x
       R_h = c_neg2*D^2 + c_neg1*D  if D < 0  else  c_pos*D,
       D = clip(root_z - h0, lo, hi)
-    where vx is the world x-velocity of the root origin, up_z the world z
-    component of the root's z axis and head_x the world x component of the
-    root's x axis (appendix A.3 reward shapes).
+    where, with a free root, vx is the world x-velocity of the root origin,
+    root_z = q[2], up_z the world z component of the root's z axis and head_x
+    the world x component of the root's x axis; without one (planar models on
+    x / z slide joints) vx = qd[vx_dof] and root_z = q[height_q], each term
+    dropped when its index is -1 (appendix A.3 reward shapes).
     """
 
     name: str
@@ -90,6 +92,8 @@ class ArticulationModel:
     rw_qd: np.ndarray           # f32 [nv]
     reward_coef: np.ndarray     # f32 [10]
     root_z: float = 1.0         # initial root height of the standing pose
+    height_q: int = -1          # q index of the root height (models without a free root)
+    vx_dof: int = -1            # qd index of the forward velocity (models without a free root)
 
     @property
     def n_links(self) -> int:
@@ -254,7 +258,8 @@ class _Builder:
 
     def finish(self, *, act_dof, act_gear, dt, substeps, ke=0.0, kd=0.0, kt=0.0, mu=0.0,
                k_limit=0.0, armature=0.0, damping=0.0, rw_q=None, rw_qd=None,
-               reward_coef=None, gravity=(0.0, 0.0, -9.81), root_z=1.0) -> ArticulationModel:
+               reward_coef=None, gravity=(0.0, 0.0, -9.81), root_z=1.0, height_q=-1,
+               vx_dof=-1) -> ArticulationModel:
         f32 = np.float32
         L = len(self.links)
         jt = np.array([l["jtype"] for l in self.links], np.int32)
@@ -308,6 +313,8 @@ class _Builder:
             rw_qd=np.zeros(nv, f32) if rw_qd is None else np.asarray(rw_qd, f32),
             reward_coef=rc,
             root_z=float(root_z),
+            height_q=int(height_q),
+            vx_dof=int(vx_dof),
         )
 
 
@@ -367,6 +374,82 @@ def ant(substeps: int = 16, density: float = ANT_DENSITY) -> ArticulationModel:
                     substeps=substeps, ke=4e4, kd=1e3, kt=1e3, mu=0.75,
                     rw_q=np.zeros(nq), root_z=-foot_z - ANT_FOOT_PENETRATION,
                     reward_coef=_loco_coef(0.0, 1.0, 0.1, 1.0, 0.27, -BIG, BIG, 0.0, 1.0, 1.0))
+
+
+PLANAR_DENSITY = 1000.0
+PLANAR_ARMATURE = 0.05     # joint armature (kg m^2), not stated by the paper
+PLANAR_DAMPING = 1.0       # joint damping (N m s/rad), not stated by the paper
+
+
+def _planar_root(b, z0, torso_p0, torso_p1, radius):
+    """Planar root: slide along world x, slide along world z (frame at height
+    z0, so q[1] is the height change from the initial pose), hinge about y
+    carrying the torso capsule.  Returns the torso link."""
+    sx = b.link(-1, PRISMATIC, axis=(1, 0, 0))
+    sz = b.link(sx, PRISMATIC, axis=(0, 0, 1), pos=(0, 0, z0))
+    m, c, I = capsule_mass_inertia(radius, torso_p0, torso_p1, PLANAR_DENSITY)
+    return b.link(sz, REVOLUTE, axis=(0, 1, 0), mass=m, com=c, inertia=I)
+
+
+def _planar_limb(b, parent, pos, p1, radius, limit):
+    """Hinge about y at pos (parent frame) with a capsule from its origin to p1."""
+    m, c, I = capsule_mass_inertia(radius, (0, 0, 0), p1, PLANAR_DENSITY)
+    return b.link(parent, REVOLUTE, axis=(0, 1, 0), pos=pos, mass=m, com=c, inertia=I, limit=limit)
+
+
+def halfcheetah(substeps: int = 16) -> ArticulationModel:
+    """Planar two-legged runner (stand-in for appendix A.3 HalfCheetah): x / z
+    slides and a pitch hinge carrying a 1 m torso capsule (radius 0.05), and
+    per leg a thigh (0.25 m), shin (0.25 m) and forward foot (0.15 m) on y
+    hinges (6 actuated DOFs, gear 100, limits +-1 rad at k_limit 1e3);
+    contact spheres at both ends of each foot and of the torso; ke 4e4,
+    kd 1e3, kt 1e3, mu 0.75.  Reward v_x - 0.1 |a|^2 (A.3); no early termination."""
+    b = _Builder("halfcheetah")
+    r = 0.05
+    z0 = 0.5 + r - 0.002
+    torso = _planar_root(b, z0, (-0.5, 0, 0), (0.5, 0, 0), r)
+    for x in (-0.5, 0.5):
+        thigh = _planar_limb(b, torso, (x, 0, 0), (0, 0, -0.25), r, (-1.0, 1.0))
+        shin = _planar_limb(b, thigh, (0, 0, -0.25), (0, 0, -0.25), r, (-1.0, 1.0))
+        foot = _planar_limb(b, shin, (0, 0, -0.25), (0.15, 0, 0), r, (-1.0, 1.0))
+        b.contact(foot, (0, 0, 0), r)
+        b.contact(foot, (0.15, 0, 0), r)
+    b.contact(torso, (-0.5, 0, 0), r)
+    b.contact(torso, (0.5, 0, 0), r)
+    return b.finish(act_dof=list(range(3, 9)), act_gear=[100.0] * 6, dt=CONTROL_DT, substeps=substeps,
+                    ke=4e4, kd=1e3, kt=1e3, mu=0.75, k_limit=1e3, armature=PLANAR_ARMATURE,
+                    damping=PLANAR_DAMPING, root_z=z0, height_q=1, vx_dof=0,
+                    reward_coef=_loco_coef(0.1, 1.0, 0.0, 0.0, 0.0, -BIG, BIG, 0.0, 0.0, 0.0))
+
+
+def hopper(substeps: int = 16) -> ArticulationModel:
+    """Planar one-legged hopper (stand-in for appendix A.3 Hopper): x / z
+    slides and a pitch hinge carrying a 0.4 m upright torso capsule (radius
+    0.05), then thigh (0.45 m), leg (0.5 m) and a horizontal foot (0.39 m) on y
+    hinges (3 actuated DOFs, gear 200, limits +-1 rad at k_limit 1e3); contact
+    spheres at both foot ends, the knee and the top of the torso.  Reward (A.3): v_x + R_height + R_angle -
+    0.1 |a|^2 with R_height = -200 D^2 (D < 0), D (D >= 0),
+    D = clip(h + 0.3, -1, 0.3), h the height change of the root, and
+    R_angle = -(theta / 30 deg)^2 (the paper's constant 1 is dropped: it does
+    not change any gradient)."""
+    b = _Builder("hopper")
+    r = 0.05
+    z0 = 0.95 + r - 0.002
+    torso = _planar_root(b, z0, (0, 0, 0), (0, 0, 0.4), r)
+    thigh = _planar_limb(b, torso, (0, 0, 0), (0, 0, -0.45), r, (-1.0, 1.0))
+    leg = _planar_limb(b, thigh, (0, 0, -0.45), (0, 0, -0.5), r, (-1.0, 1.0))
+    m, c, I = capsule_mass_inertia(r, (-0.13, 0, 0), (0.26, 0, 0), PLANAR_DENSITY)
+    foot = b.link(leg, REVOLUTE, axis=(0, 1, 0), pos=(0, 0, -0.5), mass=m, com=c, inertia=I, limit=(-1.0, 1.0))
+    b.contact(foot, (-0.13, 0, 0), r)
+    b.contact(foot, (0.26, 0, 0), r)
+    b.contact(leg, (0, 0, 0), r)
+    b.contact(torso, (0, 0, 0.4), r)
+    rw_q = np.zeros(6)
+    rw_q[2] = 1.0 / (math.pi / 6) ** 2
+    return b.finish(act_dof=[3, 4, 5], act_gear=[200.0] * 3, dt=CONTROL_DT, substeps=substeps,
+                    ke=4e4, kd=1e3, kt=1e3, mu=0.75, k_limit=1e3, armature=PLANAR_ARMATURE,
+                    damping=PLANAR_DAMPING, root_z=z0, height_q=1, vx_dof=0, rw_q=rw_q,
+                    reward_coef=_loco_coef(0.1, 1.0, 0.0, 0.0, -0.3, -1.0, 0.3, -200.0, 0.0, 1.0))
 
 
 HUMANOID_TOTAL_MASS = 40.0
@@ -558,6 +641,10 @@ def initial_state(model: ArticulationModel, n_envs: int, seed: int = 0,
     if model.name == "cartpole":
         q[:] = rng.uniform(-0.1, 0.1, size=(nq, n_envs))
         qd[:] = rng.uniform(-0.1, 0.1, size=(nv, n_envs))
+    elif int(model.joint_type[0]) != FREE:   # planar: x, z (height change), pitch, joints
+        rng_j = 0.1 if joint_range is None else joint_range
+        q[2:] = rng.uniform(-rng_j, rng_j, size=(nq - 2, n_envs))
+        qd[:] = rng.uniform(-0.1, 0.1, size=(nv, n_envs))
     else:
         rng_j = 0.2 if model.name == "ant" else 0.1
         if joint_range is not None:
@@ -627,16 +714,23 @@ def workload(name: str, scale: float = 1.0) -> Workload:
         return Workload(name, [(cartpole(), n(4096)), (ant(), n(2048)), (humanoid(), n(1024))])
     if name == "mtu-512":
         return Workload(name, [(mtu(), n(512))])
+    if name == "halfcheetah-2048":
+        return Workload(name, [(halfcheetah(), n(2048))])
+    if name == "hopper-2048":
+        return Workload(name, [(hopper(), n(2048))])
     raise KeyError(name)
 
 
-WORKLOADS = ["cartpole-64", "ant-2048", "humanoid-1024", "hetero-4096-2048-1024", "mtu-512"]
+WORKLOADS = ["cartpole-64", "ant-2048", "humanoid-1024", "hetero-4096-2048-1024", "mtu-512", "halfcheetah-2048",
+             "hopper-2048"]
 
 # Episode rules of the tasks (appendix A.3): root height below which the task
 # terminates early (-inf: no early termination) and the task horizon in control
 # steps.  The root of the ant-like model is the torso, of the humanoid-like model
-# the torso, of the muscle model the pelvis.
-EPISODE_RULES = {"cartpole": (-np.inf, 240), "ant": (0.27, 1000), "humanoid": (0.74, 1000), "mtu": (0.46, 1000)}
+# the torso, of the muscle model the pelvis; the planar models' root height is
+# the height change of their z slide.
+EPISODE_RULES = {"cartpole": (-np.inf, 240), "ant": (0.27, 1000), "humanoid": (0.74, 1000), "mtu": (0.46, 1000),
+                 "halfcheetah": (-np.inf, 1000), "hopper": (-0.45, 1000)}
 
 
 def episode_rule(model: ArticulationModel) -> Tuple[float, int]:

@@ -63,7 +63,8 @@ def airborne(m):
 
 
 def model_by_name(name):
-    return {"cartpole": I.cartpole, "ant": I.ant, "humanoid": I.humanoid, "mtu": I.mtu}[name]()
+    return {"cartpole": I.cartpole, "ant": I.ant, "humanoid": I.humanoid, "mtu": I.mtu,
+            "halfcheetah": I.halfcheetah, "hopper": I.hopper}[name]()
 
 
 def seeded_case(model, n, seed, kind="initial"):

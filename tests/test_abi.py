@@ -56,6 +56,12 @@ def test_model_validation_on_host(lib):
     dup = I.ant().replace(act_dof=np.array([6, 6, 7, 8, 9, 10, 11, 12], np.int32))
     with pytest.raises(_lib.ShacError):
         _lib.ModelHandle(dup)
+    hp = _lib.ModelHandle(I.hopper())
+    assert (hp.nq, hp.nv, hp.na) == (6, 6, 3)
+    for kw in ({"height_q": 6}, {"vx_dof": 6}, {"height_q": -2}):   # reward coordinates out of range
+        with pytest.raises(_lib.ShacError) as e:
+            _lib.ModelHandle(I.hopper().replace(**kw))
+        assert e.value.status == 2
     assert _lib.status_string(5) == "capacity exceeded"
 
 

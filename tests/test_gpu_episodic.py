@@ -30,11 +30,16 @@ def T(x):
     return torch.from_numpy(np.ascontiguousarray(np.asarray(x, np.float32).reshape(-1))).cuda()
 
 
+def _height_index(m):
+    """q index of the root height: q[2] for a free root, else height_q."""
+    return 2 if int(m.joint_type[0]) == 0 else int(m.height_q)
+
+
 def _case(name, N, h, seed):
     """Seeded reset states, random episode counters and a short horizon so
-    both rules fire.  Free-root models fly without their contacts, started
-    from heights spread just around the task height, so that the root falls
-    through it during the window on smooth dynamics."""
+    both rules fire.  Models with a height rule fly without their contacts,
+    started from root heights spread just around the task height, so that the
+    root falls through it during the window on smooth dynamics."""
     m = getattr(I, name)()
     thr, _ = I.episode_rule(m)
     if thr > -np.inf:
@@ -42,7 +47,7 @@ def _case(name, N, h, seed):
     q0, qd0 = I.initial_state(m, N, seed)
     q0 = q0.copy()
     if thr > -np.inf:
-        q0[2] = np.linspace(thr - 0.02, thr + 0.1, N).astype(np.float32)
+        q0[_height_index(m)] = np.linspace(thr - 0.02, thr + 0.1, N).astype(np.float32)
     qr, qdr = I.initial_state(m, N, seed + 1)
     act = I.window_actions(m, N, h, seed + 2)
     H = 5
@@ -59,7 +64,7 @@ def _run(m, N, h, thr, q0, qd0, qr, qdr, act, H, ep0):
     return sim, ep, out
 
 
-@pytest.mark.parametrize("name,N", [("ant", 37), ("humanoid", 9), ("cartpole", 21)])
+@pytest.mark.parametrize("name,N", [("ant", 37), ("humanoid", 9), ("cartpole", 21), ("hopper", 13)])
 def test_episodic_window_matches_oracle_step_by_step(oracle_mod, name, N):
     h = 8
     m, thr, q0, qd0, qr, qdr, act, H, ep0 = _case(name, N, h, seed=3)
@@ -72,15 +77,15 @@ def test_episodic_window_matches_oracle_step_by_step(oracle_mod, name, N):
     o = oracle_mod.Oracle(m)
     a = act.transpose(0, 2, 1)
     e = ep0.astype(np.int64)
-    root_free = int(m.joint_type[0]) == 0
+    hq = _height_index(m) if thr > -np.inf else -1
     fired = 0
     for t in range(h):
         pq, pqd, pr = o.step(gq[t], gqd[t], a[t])
         assert_state_close(grw[t], pr, f"{name} reward step {t}")
         e = e + 1
         by_len = e >= H
-        by_height = (pq[:, 2] < thr) if root_free else np.zeros(N, bool)
-        clear = by_len | (np.abs(pq[:, 2] - thr) > MARGIN) if root_free else np.ones(N, bool)
+        by_height = (pq[:, hq] < thr) if hq >= 0 else np.zeros(N, bool)
+        clear = by_len | (np.abs(pq[:, hq] - thr) > MARGIN) if hq >= 0 else np.ones(N, bool)
         np.testing.assert_array_equal(gd[t][clear], (by_len | by_height)[clear], err_msg=f"{name} done step {t}")
         fired += int(gd[t].sum())
         d = gd[t]

@@ -36,7 +36,7 @@ def T(x):
 
 # (model name, N, airborne?) -- N chosen to leave a ragged last work item
 CASES = [("cartpole", 37, False), ("ant", 23, False), ("ant", 9, True), ("humanoid", 5, False),
-         ("humanoid", 3, True), ("mtu", 3, False)]
+         ("humanoid", 3, True), ("mtu", 3, False), ("halfcheetah", 19, False), ("hopper", 21, False)]
 
 
 @pytest.mark.parametrize("form", ["plain", "batched"])
@@ -81,7 +81,8 @@ def test_step_adjoint_matches_oracle(oracle_mod, form, name, N, air):
 
 
 WINDOW_CASES = [("cartpole", 37, False, 32), ("ant", 11, False, 32), ("ant", 5, True, 32),
-                ("humanoid", 3, False, 6), ("mtu", 2, False, 4)]
+                ("humanoid", 3, False, 6), ("mtu", 2, False, 4), ("halfcheetah", 7, False, 16),
+                ("hopper", 9, False, 16)]
 
 
 @pytest.mark.parametrize("form", ["plain", "batched"])

@@ -62,7 +62,7 @@ def test_cartpole_mass_matrix_and_bias_closed_form(oracle_mod, th, thd, xd):
     np.testing.assert_allclose(c, cref, rtol=1e-6, atol=1e-9)
 
 
-@pytest.mark.parametrize("name", ["ant", "humanoid", "mtu"])
+@pytest.mark.parametrize("name", ["ant", "humanoid", "mtu", "halfcheetah", "hopper"])
 def test_kinetic_energy_equals_half_qd_M_qd(oracle_mod, name):
     """0.5 qd^T M qd equals sum_i (0.5 m_i |v_ci|^2 + 0.5 w_i^T I_i w_i),
     the latter from link velocities (independent of the mass matrix)."""
@@ -78,7 +78,7 @@ def test_kinetic_energy_equals_half_qd_M_qd(oracle_mod, name):
         assert np.linalg.eigvalsh(M).min() > 0
 
 
-@pytest.mark.parametrize("name", ["cartpole", "ant", "humanoid", "mtu"])
+@pytest.mark.parametrize("name", ["cartpole", "ant", "humanoid", "mtu", "halfcheetah", "hopper"])
 def test_newton_euler_difference_is_mass_matrix(oracle_mod, name):
     """ID(q, qd, qdd) - ID(q, qd, 0) = M(q) qdd: ties the Newton-Euler
     recursion to the Jacobian-based mass matrix."""
@@ -353,7 +353,8 @@ def _fd_jacobian(o, q, qd, a, eps):
     return J
 
 
-@pytest.mark.parametrize("case", ["cartpole", "ant_air", "ant_contact", "humanoid_air", "mtu_air"])
+@pytest.mark.parametrize("case", ["cartpole", "ant_air", "ant_contact", "humanoid_air", "mtu_air",
+                                  "halfcheetah_contact", "hopper_air"])
 def test_step_jacobian_matches_central_differences(oracle_mod, case):
     """The exact (dual-number) step Jacobian of Eq. backward against central
     finite differences of the FP64 step, on inputs whose branch decisions
@@ -366,8 +367,14 @@ def test_step_jacobian_matches_central_differences(oracle_mod, case):
         q, qd = I.initial_state(m, 1, seed=3)
         q[2] -= 0.01      # every foot well inside the contact branch
         qd[3:5] = 1.0     # saturated friction at the feet
+    elif case == "halfcheetah_contact":
+        m = I.halfcheetah(substeps=4)
+        q, qd = I.initial_state(m, 1, seed=3, joint_range=0.0)
+        q[1] -= 0.01      # the four foot spheres well inside the contact branch, torso ends above
+        qd[:] = 0.0
+        qd[0] = 1.0       # saturated friction at the feet
     else:
-        base = {"ant_air": I.ant, "humanoid_air": I.humanoid, "mtu_air": I.mtu}[case]()
+        base = {"ant_air": I.ant, "humanoid_air": I.humanoid, "mtu_air": I.mtu, "hopper_air": I.hopper}[case]()
         m = base.replace(contact_link=base.contact_link[:0], contact_pos=base.contact_pos[:0],
                          contact_radius=base.contact_radius[:0], substeps=4,
                          q_lower=np.full_like(base.q_lower, -I.BIG), q_upper=np.full_like(base.q_upper, I.BIG))
@@ -433,3 +440,24 @@ def test_reward_shapes(oracle_mod):
     oc = _orc(oracle_mod, c.replace(dt=1e-12, gravity=np.zeros(3, np.float32)))
     _, _, r = oc.step(np.array([[0.2, -0.3]]), np.zeros((1, 2)), np.zeros((1, 1)))
     np.testing.assert_allclose(r[0], -(0.09 + 0.1 * 0.04), atol=1e-9)
+
+
+def test_planar_reward_shapes(oracle_mod):
+    """Appendix A.3 HalfCheetah v_x - 0.1 |a|^2 and Hopper v_x + R_height +
+    R_angle - 0.1 |a|^2 at states where every term is known (no gravity,
+    vanishing step): hopper height change -0.4 gives D = clip(-0.1) and
+    R_height = -200 D^2 = -2; pitch 0.2 gives R_angle = -(0.2 / (pi / 6))^2;
+    at height change +0.5, D clips to 0.3."""
+    def still(m):
+        m = m.replace(dt=1e-12, gravity=np.zeros(3, np.float32))
+        return _orc(oracle_mod, m.replace(contact_link=m.contact_link[:0], contact_pos=m.contact_pos[:0],
+                                          contact_radius=m.contact_radius[:0]))
+    oc = still(I.halfcheetah(substeps=1))
+    qd = np.zeros((1, 9)); qd[0, 0] = 1.5
+    _, _, r = oc.step(np.zeros((1, 9)), qd, np.full((1, 6), 0.5))
+    np.testing.assert_allclose(r[0], 1.5 - 0.1 * 6 * 0.25, atol=1e-6)
+    oh = still(I.hopper(substeps=1))
+    q = np.zeros((2, 6)); q[0, 1] = -0.4; q[0, 2] = 0.2; q[1, 1] = 0.5
+    qd = np.zeros((2, 6)); qd[:, 0] = 1.5
+    _, _, r = oh.step(q, qd, np.full((2, 3), 0.5))
+    np.testing.assert_allclose(r, [1.5 - 2.0 - (0.2 / (math.pi / 6)) ** 2 - 0.075, 1.5 + 0.3 - 0.075], atol=1e-6)

@@ -49,22 +49,24 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # Algorithmic FP32 work per env-step, measured (not estimated): thread-level
 # FADD + FMUL + 2 x FFMA executed by the one-environment-per-thread (PLAIN)
 # stage kernels over one window step, counted by ncu (the command and the
-# per-stage split are in profiles/plain_flops_ant.md).  The batched adjoint
-# recomputes a step's substeps once, so its count is one forward recompute
-# plus the reverse-only stages.  Workloads without a count report achieved=null.
+# per-stage split are in profiles/plain_flops_ant.md).  The timed batched
+# window keeps its substep records (window tape), so the adjoint kernel does
+# the reverse-only stages; the recomputing adjoint would add one forward
+# recompute (134,556).  Workloads without a count report achieved=null.
 ALGO_FLOPS_PER_ENV_STEP = {
-    "ant-2048": {"forward": 134692, "adjoint": 134556 + 172338},
+    "ant-2048": {"forward": 134692, "adjoint": 172338},
 }
 
 # DRAM traffic (read + write) per launch of each batched kernel at h = 32 on
 # ant-2048, scaled from an ncu capture at h = 2 by the 16x env-steps (the
 # per-step traffic is the same at every step); profiles/batched_ant_2048.md.
-TRAFFIC_BYTES_PER_LAUNCH = {"ant-2048": {"k_batched_forward": 16 * (0.477696e6 + 0.0),
-                                         "k_batched_adjoint": 16 * (6.149632e6 + 105.850368e6)}}
+TRAFFIC_BYTES_PER_LAUNCH = {}   # re-taken on the window-tape kernels below
 
 # Algorithmic HBM bytes per env-step (ant): forward reads the action (8 f32)
 # and writes the checkpoint (29) and reward (1); the adjoint reads checkpoint
 # (29), action (8) and reward cotangent (1) and writes the action cotangent (8).
+# With the window tape both kernels add the tape bytes of an env-step (written
+# by the forward, read by the adjoint), measured from the workspace size.
 ALGO_BYTES_PER_ENV_STEP = {"k_batched_forward": 4 * (8 + 29 + 1), "k_batched_adjoint": 4 * (29 + 8 + 1 + 8)}
 
 
@@ -300,6 +302,9 @@ def gpu_main(args, rank, world, dist):
         return Simulator(groups, form=form, h_max=H)
 
     sim = make("batched")
+    ws_recompute = sim.workspace.numel()
+    sim.set_window_tape(True)   # the forward keeps every substep record; the adjoint reads them back
+    tape_bytes = (sim.workspace.numel() - ws_recompute) / (H * (n_envs + 31 * len(groups)))
     seed = shard_seed(rank)
     q0 = sim.pack([I.initial_state(m, n, seed)[0] for m, n in groups], "q")
     qd0 = sim.pack([I.initial_state(m, n, seed)[1] for m, n in groups], "qd")
@@ -362,6 +367,22 @@ def gpu_main(args, rank, world, dist):
 
     ms_fwd = timed(one_fwd, max(3, args.steps // 2), 1)
     ms_adj = timed(one_adj, max(3, args.steps // 2), 1)
+
+    # ---- the same window with the recomputing adjoint (no window tape)
+    rsim = make("batched")
+    with torch.cuda.stream(stream):
+        rof = rsim.window_forward(q0, qd0, act, stream=stream)
+        roa = rsim.window_adjoint(rof[0], rof[1], act, rbar, zq, zqd, stream=stream)
+    stream.synchronize()
+    rgraph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(stream):
+        with torch.cuda.graph(rgraph, stream=stream):
+            rsim.window_forward(q0, qd0, act, out=rof, stream=stream)
+            rsim.window_adjoint(rof[0], rof[1], act, rbar, zq, zqd, out=roa, stream=stream)
+    stream.synchronize()
+    ms_recompute = timed(rgraph.replay, args.steps, args.warmup)
+    same = all(torch.equal(x, y) for x, y in zip(tuple(rof) + tuple(roa), tuple(outf) + tuple(outa)))
+    del rgraph, rsim
 
     # ---- episodic window (early termination with in-kernel reset, gradient
     # cut at resets), graph captured like the main window: the task heights and
@@ -429,8 +450,8 @@ def gpu_main(args, rank, world, dist):
     d2h = 4 * (hrew.numel() + hab.numel() + hq0b.numel() + hqd0b.numel())
 
     # max over ranks
-    ms_batched, ms_plain, ms_e2e, ms_fwd, ms_adj, ms_episodic = max_over_ranks(
-        [ms_batched, ms_plain, ms_e2e, ms_fwd, ms_adj, ms_episodic], dist, dev)
+    ms_batched, ms_plain, ms_e2e, ms_fwd, ms_adj, ms_episodic, ms_recompute = max_over_ranks(
+        [ms_batched, ms_plain, ms_e2e, ms_fwd, ms_adj, ms_episodic, ms_recompute], dist, dev)
     if rank != 0:
         return
     env_steps = n_envs * H * world
@@ -446,13 +467,18 @@ def gpu_main(args, rank, world, dist):
         "warmup": args.warmup, "ms_per_step": ms_batched, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": wl.name, "n_envs_per_gpu": n_envs, "h": H,
-                   "substeps": groups[0][0].substeps, "form": "batched, forward+adjoint captured in one CUDA graph",
+                   "substeps": groups[0][0].substeps,
+                   "form": "batched, forward+adjoint captured in one CUDA graph, window tape kept in HBM",
+                   "tape_bytes_per_env_step": tape_bytes,
                    "lanes_per_env": [sim.get_launch(g)[0] for g in range(len(groups))],
                    "warps_per_cta": sim.get_launch(0)[1], "l2": "flushed (256 MB write) before each timed step",
                    "parallelism": f"env-sharded replicas x{world}"},
         "plain_form": {"value": plain_value, "unit": "env-steps/s", "ms_per_step": ms_plain,
                        "steps": args.plain_steps},
         "speedup_vs_plain": value / plain_value,
+        "recompute_window": {"value": env_steps / (ms_recompute * 1e-3), "unit": "env-steps/s",
+                             "ms_per_step": ms_recompute, "bitwise_equal_to_taped": bool(same),
+                             "note": "adjoint recomputes each step's substeps instead of reading the window tape"},
         "episodic": {"value": env_steps / (ms_episodic * 1e-3), "unit": "env-steps/s", "ms_per_step": ms_episodic,
                      "done_frac": done_frac,
                      "rule": "root below the task height or the task horizon; seeded reset states; "
@@ -467,7 +493,7 @@ def gpu_main(args, rank, world, dist):
                      "unit": "TFLOP/s", "frac": None if achieved is None else achieved / FP32_PEAK_TFLOPS,
                      "peak_source": "derived FP32 peak: 152 SMs x 128 lanes x 2 x 2.07 GHz",
                      "traffic": traffic, "algo_flops_per_env_step": af,
-                     "algo_bytes_per_env_step": ALGO_BYTES_PER_ENV_STEP.get(dominant)},
+                     "algo_bytes_per_env_step": ALGO_BYTES_PER_ENV_STEP.get(dominant, 0) + tape_bytes},
     }
     if not args.no_cpu_baseline:
         r, n, hs, threads, dt = oracle_window_rate(groups[0][0], groups[0][1], seed=0, target_s=12.0)

@@ -266,6 +266,23 @@ shac_status shac_batch_set_launch(shac_batch* batch, int32_t group, int32_t lane
 shac_status shac_batch_get_launch(const shac_batch* batch, int32_t group, int32_t* lanes_per_env,
                                   int32_t* warps_per_cta);
 
+/* Window tape (BATCHED form; SHAC_ERR_UNSUPPORTED for PLAIN): keep = 1 makes
+ * shac_window_forward (and its episodic variant) store every substep record of
+ * every step (link poses, inertias, subspaces, velocities, external wrenches,
+ * contact items, Cholesky factor, accelerations) and each step's post-step state
+ * in the workspace, and shac_window_adjoint (episodic too) read them back instead
+ * of recomputing each step's substeps: the reverse pass skips one forward
+ * recompute, at K * record + nq + nv floats per env-step of workspace (ant-like
+ * model, h_max = 32, 2048 environments: 2.9 GB; shac_batch_workspace_bytes
+ * reports the new size, reallocate after the call).  Contract: the adjoint
+ * window must follow the forward window on the same workspace with the same h,
+ * q_traj/qd_traj, act (and done mask), with no other window call in between; it
+ * then returns what the recomputing adjoint returns, bit for bit.  Step-level
+ * calls (shac_step, shac_step_adjoint, shac_step_adjoint_static) never use the
+ * tape.  keep = 0 (the default) recomputes.  (Sec. 3.1 keeps each substep's
+ * Cholesky factor for the backward pass; the tape keeps every intermediate.) */
+shac_status shac_batch_set_window_tape(shac_batch* batch, int32_t keep);
+
 /* Synchronises the stream and returns the sticky device flags
  * (bit 0: non-finite state); clear != 0 resets them.  Not capturable. */
 shac_status shac_get_status(shac_batch* batch, void* stream, uint32_t* sticky_flags, int32_t clear);

@@ -45,6 +45,11 @@ struct shac_batch {
   // workspace layout (bytes)
   size_t ws_counter = 0, ws_tape = 0, ws_plain = 0, ws_total = 0;
   std::vector<size_t> plain_scratch_off, plain_tape_off, batched_tape_off;
+  // window tape (batched): every step's substep records kept by the forward window
+  int window_tape = 0;
+  size_t ws_step = 0;                    // bytes the step-level calls use (a prefix of the workspace)
+  std::vector<size_t> window_tape_off;   // bytes
+  std::vector<int64_t> window_tape_step; // floats per step per environment slot
 };
 
 static shac_status cuda_ok(cudaError_t e) { return e == cudaSuccess ? SHAC_OK : SHAC_ERR_CUDA; }
@@ -395,6 +400,18 @@ static void compute_workspace(shac_batch* b) {
       off = align(off + REC * (size_t)(g.N + 31) * sizeof(float));
     }
   }
+  b->ws_step = off;
+  b->window_tape_off.assign(b->groups.size(), 0);
+  b->window_tape_step.assign(b->groups.size(), 0);
+  if (b->form == SHAC_FORM_BATCHED && b->window_tape) {
+    // h_max steps x (K records + post-step q, qd) per environment slot
+    for (size_t gi = 0; gi < b->groups.size(); ++gi) {
+      const shac_model* m = b->groups[gi].m;
+      b->window_tape_step[gi] = (int64_t)m->layout.rec_floats * m->K + m->nq + m->nv;
+      b->window_tape_off[gi] = off;
+      off = align(off + (size_t)b->window_tape_step[gi] * b->h_max * (size_t)(b->groups[gi].N + 31) * sizeof(float));
+    }
+  }
   b->ws_total = off;
 }
 
@@ -481,6 +498,14 @@ extern "C" shac_status shac_batch_set_launch(shac_batch* b, int32_t group, int32
   return build_items(b);
 }
 
+extern "C" shac_status shac_batch_set_window_tape(shac_batch* b, int32_t keep) {
+  if (!b || (keep != 0 && keep != 1)) return SHAC_ERR_INVALID_ARG;
+  if (keep && b->form != SHAC_FORM_BATCHED) return SHAC_ERR_UNSUPPORTED;
+  b->window_tape = keep;
+  compute_workspace(b);
+  return SHAC_OK;
+}
+
 extern "C" shac_status shac_batch_get_launch(const shac_batch* b, int32_t group, int32_t* lanes, int32_t* warps) {
   if (!b || group < 0 || group >= (int)b->groups.size()) return SHAC_ERR_INVALID_ARG;
   if (lanes) *lanes = b->groups[group].lanes;
@@ -499,7 +524,8 @@ static PlainGroup plain_group(const shac_batch* b, int gi, void* ws) {
   return p;
 }
 
-static shac_status batched_launch(shac_batch* b, BatchedArgs& a, void* ws, cudaStream_t s, bool adjoint) {
+static shac_status batched_launch(shac_batch* b, BatchedArgs& a, void* ws, cudaStream_t s, bool adjoint,
+                                  bool window = false) {
   a.models = b->d_models;
   a.n_groups = (int)b->groups.size();
   a.io = b->io;
@@ -514,6 +540,14 @@ static shac_status batched_launch(shac_batch* b, BatchedArgs& a, void* ws, cudaS
   a.counter = reinterpret_cast<int*>(static_cast<char*>(ws) + b->ws_counter);
   a.tape = reinterpret_cast<float*>(ws);
   for (int gi = 0; gi < a.n_groups; ++gi) a.tape_off[gi] = (int64_t)(b->batched_tape_off[gi] / sizeof(float));
+  if (window && b->window_tape) {
+    a.tape_window = 1;
+    a.tape_hmax = b->h_max;
+    for (int gi = 0; gi < a.n_groups; ++gi) {
+      a.tape_off[gi] = (int64_t)(b->window_tape_off[gi] / sizeof(float));
+      a.tape_step[gi] = b->window_tape_step[gi];
+    }
+  }
   a.flags = b->d_flags;
   if (b->n_items == 0) return SHAC_OK;
   const int W = batched_warps(b);
@@ -556,7 +590,7 @@ static void set_episodic(const shac_batch* b, BatchedArgs& a, const Episodic* ep
 
 static shac_status run_forward(shac_batch* b, cudaStream_t s, void* ws, int h, const float* q0, const float* qd0,
                                const float* act, float* q_out, float* qd_out, float* reward, float* q_copy0,
-                               float* qd_copy0, const Episodic* ep = nullptr) {
+                               float* qd_copy0, const Episodic* ep = nullptr, bool window = false) {
   if (b->form == SHAC_FORM_BATCHED) {
     BatchedArgs a{};
     a.h = h;
@@ -564,8 +598,7 @@ static shac_status run_forward(shac_batch* b, cudaStream_t s, void* ws, int h, c
     a.q_out = q_out; a.qd_out = qd_out; a.reward = reward;
     a.q_copy0 = q_copy0; a.qd_copy0 = qd_copy0;
     set_episodic(b, a, ep);
-    // per-group tape offsets are not used by the forward kernel
-    return batched_launch(b, a, ws, s, false);
+    return batched_launch(b, a, ws, s, false, window);
   }
   if (ep) return SHAC_ERR_UNSUPPORTED;
   if (q_copy0) {
@@ -594,7 +627,7 @@ static shac_status run_forward(shac_batch* b, cudaStream_t s, void* ws, int h, c
 static shac_status run_adjoint(shac_batch* b, cudaStream_t s, void* ws, int h, const float* q_traj,
                                const float* qd_traj, const float* act, const float* reward_bar, const float* qtb,
                                const float* qdtb, const float* qT_bar, const float* qdT_bar, float* q0_bar,
-                               float* qd0_bar, float* act_bar, const Episodic* ep = nullptr) {
+                               float* qd0_bar, float* act_bar, const Episodic* ep = nullptr, bool window = false) {
   if (b->form == SHAC_FORM_BATCHED) {
     BatchedArgs a{};
     a.h = h;
@@ -602,7 +635,7 @@ static shac_status run_adjoint(shac_batch* b, cudaStream_t s, void* ws, int h, c
     a.qT_bar = qT_bar; a.qdT_bar = qdT_bar; a.qtb = qtb; a.qdtb = qdtb;
     a.q0_bar = q0_bar; a.qd0_bar = qd0_bar; a.act_bar = act_bar;
     set_episodic(b, a, ep);
-    return batched_launch(b, a, ws, s, true);
+    return batched_launch(b, a, ws, s, true, window);
   }
   if (ep) return SHAC_ERR_UNSUPPORTED;
   for (int gi = 0; gi < (int)b->groups.size(); ++gi) {
@@ -660,7 +693,7 @@ extern "C" shac_status shac_window_forward(shac_batch* b, void* stream, void* ws
   if (!b || !aligned_ws(b, ws) || h < 1 || h > b->h_max || !q0 || !qd0 || !act || !q_traj || !qd_traj || !reward)
     return SHAC_ERR_INVALID_ARG;
   return run_forward(b, (cudaStream_t)stream, ws, h, q0, qd0, act, q_traj + b->q_size, qd_traj + b->qd_size, reward,
-                     q_traj, qd_traj);
+                     q_traj, qd_traj, nullptr, true);
 }
 
 extern "C" shac_status shac_window_adjoint(shac_batch* b, void* stream, void* ws, int32_t h, const float* q_traj,
@@ -672,7 +705,7 @@ extern "C" shac_status shac_window_adjoint(shac_batch* b, void* stream, void* ws
     return SHAC_ERR_INVALID_ARG;
   return run_adjoint(b, (cudaStream_t)stream, ws, h, q_traj, qd_traj, act, reward_bar, q_traj_bar, qd_traj_bar,
                      q_traj_bar + (size_t)h * b->q_size, qd_traj_bar + (size_t)h * b->qd_size, q0_bar, qd0_bar,
-                     act_bar);
+                     act_bar, nullptr, true);
 }
 
 extern "C" shac_status shac_window_forward_episodic(shac_batch* b, void* stream, void* ws, int32_t h,
@@ -689,7 +722,7 @@ extern "C" shac_status shac_window_forward_episodic(shac_batch* b, void* stream,
   ep.q_reset = q_reset; ep.qd_reset = qd_reset; ep.term_height = term_height;
   ep.max_ep = max_episode_steps; ep.ep_step = episode_step; ep.done = done;
   return run_forward(b, (cudaStream_t)stream, ws, h, q0, qd0, act, q_traj + b->q_size, qd_traj + b->qd_size, reward,
-                     q_traj, qd_traj, &ep);
+                     q_traj, qd_traj, &ep, true);
 }
 
 extern "C" shac_status shac_window_adjoint_episodic(shac_batch* b, void* stream, void* ws, int32_t h,
@@ -705,7 +738,7 @@ extern "C" shac_status shac_window_adjoint_episodic(shac_batch* b, void* stream,
   ep.done_in = done;
   return run_adjoint(b, (cudaStream_t)stream, ws, h, q_traj, qd_traj, act, reward_bar, q_traj_bar, qd_traj_bar,
                      q_traj_bar + (size_t)h * b->q_size, qd_traj_bar + (size_t)h * b->qd_size, q0_bar, qd0_bar,
-                     act_bar, &ep);
+                     act_bar, &ep, true);
 }
 
 // ---------------------------------------------------------------------------
@@ -749,7 +782,7 @@ extern "C" shac_status shac_step_adjoint_static(shac_batch* b, void* stream, con
                                                 float* act_bar) {
   if (!b || !q || !qd || !act || !q_next_bar || !qd_next_bar || !reward_bar || !q_bar || !qd_bar || !act_bar)
     return SHAC_ERR_INVALID_ARG;
-  if (b->ws_total > STATIC_SCRATCH_BYTES) return SHAC_ERR_CAPACITY;
+  if (b->ws_step > STATIC_SCRATCH_BYTES) return SHAC_ERR_CAPACITY;
   void* ws = nullptr;
   const shac_status st = static_scratch_address(&ws);
   if (st != SHAC_OK) return st;

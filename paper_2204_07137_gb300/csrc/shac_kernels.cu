@@ -210,13 +210,28 @@ __device__ void forward_item(const BatchedArgs& a, const DevModel& M, const Work
   }
   int ep = 0;   // episodic window: steps since the last reset (team lane 0)
   if (a.done && t.lane == 0) ep = a.ep_step[io.env_off + t.env];
+  const int REC = M.rec_floats;
+  float* wtape = a.tape_window ? a.tape + a.tape_off[it.group] +
+                                     (size_t)(it.env0 + t.team) * a.tape_hmax * a.tape_step[it.group]
+                               : nullptr;
   for (int step = 0; step < a.h; ++step) {
     team_load(w, M.o_ACT, a.act + (size_t)step * a.io.act_size + io.act_off, M.na, io.N, t.env, t.lane, t.nl);
     clear_comp(M, w, t.lane, t.nl);
     team_sync(t.nl);
+    float* wt = wtape ? wtape + (size_t)step * a.tape_step[it.group] : nullptr;
     for (int k = 0; k < M.K; ++k) {
       substep_dynamics(M, w, t.lane, t.nl, nm);
+      if (wt) {   // keep the substep record for the adjoint
+        float* rec = wt + (size_t)k * REC;
+        for (int j = t.lane; j < REC; j += t.nl) rec[j] = w[j];
+        team_sync(t.nl);
+      }
       st_integrate(M, w, t.lane, t.nl);
+    }
+    if (wt) {     // post-step state (before any reset): the reward adjoint's input
+      float* post = wt + (size_t)M.K * REC;
+      for (int j = t.lane; j < M.nq; j += t.nl) post[j] = w[M.o_Q + j];
+      for (int j = t.lane; j < M.nv; j += t.nl) post[M.nq + j] = w[M.o_QD + j];
     }
     if (t.lane == 0 && t.active) {
       a.reward[(size_t)step * a.io.n_envs + io.env_off + t.env] = reward_value(M, w);
@@ -261,7 +276,9 @@ __device__ __forceinline__ void record_load(const SMem& w, const float* src, int
 // One work item of the window adjoint (reverse over steps).  Each step's
 // substeps are recomputed once from its checkpoint; every substep's record
 // (start state and forward intermediates, scratch [0, rec_floats)) is kept in
-// the workspace and reloaded by the reverse pass.
+// the workspace and reloaded by the reverse pass.  With the window tape the
+// forward window already kept every record (and the post-step state), and the
+// recompute is skipped.
 __device__ void adjoint_item(const BatchedArgs& a, const DevModel& M, const WorkItem& it, const SMem& w,
                              const Team& t) {
   const int nm = a.dense_nm[it.group];
@@ -282,17 +299,27 @@ __device__ void adjoint_item(const BatchedArgs& a, const DevModel& M, const Work
     }
     clear_comp(M, w, t.lane, t.nl);
     team_sync(t.nl);
-    for (int k = 0; k < M.K; ++k) {
-      substep_dynamics(M, w, t.lane, t.nl, nm);
-      float* rec = tape + (size_t)k * REC;
-      for (int j = t.lane; j < REC; j += t.nl) rec[j] = w[j];
+    const float* recs = tape;   // this step's substep records
+    if (a.tape_window) {        // kept by the forward window: the post-step state is read back
+      recs = a.tape + a.tape_off[it.group] +
+             ((size_t)(it.env0 + t.team) * a.tape_hmax + step) * a.tape_step[it.group];
+      const float* post = recs + (size_t)M.K * REC;
+      for (int j = t.lane; j < M.nq; j += t.nl) w[M.o_Q + j] = post[j];
+      for (int j = t.lane; j < M.nv; j += t.nl) w[M.o_QD + j] = post[M.nq + j];
       team_sync(t.nl);
-      st_integrate(M, w, t.lane, t.nl);
+    } else {                    // recomputed once from the checkpoint
+      for (int k = 0; k < M.K; ++k) {
+        substep_dynamics(M, w, t.lane, t.nl, nm);
+        float* rec = tape + (size_t)k * REC;
+        for (int j = t.lane; j < REC; j += t.nl) rec[j] = w[j];
+        team_sync(t.nl);
+        st_integrate(M, w, t.lane, t.nl);
+      }
     }
     if (t.lane == 0) reward_adjoint(M, w, a.reward_bar[(size_t)step * a.io.n_envs + io.env_off + t.env]);
     team_sync(t.nl);
     for (int k = M.K - 1; k >= 0; --k) {
-      record_load(w, tape + (size_t)k * REC, REC, t.lane, t.nl);
+      record_load(w, recs + (size_t)k * REC, REC, t.lane, t.nl);
       team_sync(t.nl);
       st_integrate_adj(M, w, t.lane, t.nl);
       st_dynamics_adj(M, w, t.lane, t.nl, nm);

@@ -37,6 +37,11 @@ struct BatchedArgs {
   int* counter;             // work counter (zeroed before each launch)
   float* tape;              // substep tape base (workspace)
   int64_t tape_off[MAX_GROUPS];   // per-group float offset; slot per env (N_g + 31 slots)
+  // window tape: the forward keeps every step's substep records and post-step
+  // state, the adjoint reads them instead of recomputing (0: recompute)
+  int tape_window;
+  int tape_hmax;                  // steps per environment slot
+  int64_t tape_step[MAX_GROUPS];  // floats per step: K records + post-step q, qd
   unsigned int* flags;
   int h;
   // window / step buffers

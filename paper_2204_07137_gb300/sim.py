@@ -67,6 +67,13 @@ class Simulator:
                    "shac_batch_set_launch")
         self._alloc_workspace()
 
+    def set_window_tape(self, keep: bool = True):
+        """Keep every substep record of the forward window for the window
+        adjoint (no recompute; much larger workspace; see shacsim.h for the
+        contract: the adjoint must follow its forward on the same buffers)."""
+        _lib.check(_lib.load().shac_batch_set_window_tape(self.batch, int(bool(keep))), "shac_batch_set_window_tape")
+        self._alloc_workspace()
+
     def get_launch(self, group: int) -> Tuple[int, int]:
         l, w = ctypes.c_int32(), ctypes.c_int32()
         _lib.check(_lib.load().shac_batch_get_launch(self.batch, group, ctypes.byref(l), ctypes.byref(w)),

@@ -84,6 +84,7 @@ static void compute_layout(shac_model* m) {
   take(d.o_Q, m->nq); take(d.o_QD, nv); take(d.o_R, 9 * L); take(d.o_P, 3 * L); take(d.o_SI, 10 * L);
   take(d.o_S, 6 * nv); take(d.o_V, 6 * L); take(d.o_FX, 6 * L); take(d.o_IT, 7 * ni);
   take(d.o_M, nv * nv); take(d.o_LD, nv); take(d.o_QDD, nv);
+  o = (o + 3) / 4 * 4;   // records are copied 16 bytes at a time
   d.rec_floats = o;
   take(d.o_ACT, m->na); take(d.o_QB, m->nq); take(d.o_QDB, nv); take(d.o_ACTB, m->na);
   take(d.o_QC, m->nq); take(d.o_QDC, nv); take(d.o_A, 6 * L); take(d.o_F, 6 * L); take(d.o_IC, 10 * L);
@@ -407,7 +408,7 @@ static void compute_workspace(shac_batch* b) {
     // h_max steps x (K records + post-step q, qd) per environment slot
     for (size_t gi = 0; gi < b->groups.size(); ++gi) {
       const shac_model* m = b->groups[gi].m;
-      b->window_tape_step[gi] = (int64_t)m->layout.rec_floats * m->K + m->nq + m->nv;
+      b->window_tape_step[gi] = ((int64_t)m->layout.rec_floats * m->K + m->nq + m->nv + 3) / 4 * 4;
       b->window_tape_off[gi] = off;
       off = align(off + (size_t)b->window_tape_step[gi] * b->h_max * (size_t)(b->groups[gi].N + 31) * sizeof(float));
     }

@@ -197,6 +197,13 @@ __device__ __forceinline__ void setup_team(const BatchedArgs& a, const WorkItem&
   t.env = it.env0 + (t.active ? t.team : 0);
 }
 
+// Copy a substep record (n floats, a multiple of 4) from scratch to its
+// 16-byte aligned slot in the workspace, 16 bytes per store.
+__device__ __forceinline__ void record_save(float* dst, const SMem& w, int n, int lane, int nl) {
+  float4* d4 = reinterpret_cast<float4*>(dst);
+  for (int j = lane; j < n / 4; j += nl) d4[j] = make_float4(w[4 * j], w[4 * j + 1], w[4 * j + 2], w[4 * j + 3]);
+}
+
 // One work item of the forward window (all steps, all substeps).
 __device__ void forward_item(const BatchedArgs& a, const DevModel& M, const WorkItem& it, const SMem& w,
                              const Team& t) {
@@ -222,8 +229,7 @@ __device__ void forward_item(const BatchedArgs& a, const DevModel& M, const Work
     for (int k = 0; k < M.K; ++k) {
       substep_dynamics(M, w, t.lane, t.nl, nm);
       if (wt) {   // keep the substep record for the adjoint
-        float* rec = wt + (size_t)k * REC;
-        for (int j = t.lane; j < REC; j += t.nl) rec[j] = w[j];
+        record_save(wt + (size_t)k * REC, w, REC, t.lane, t.nl);
         team_sync(t.nl);
       }
       st_integrate(M, w, t.lane, t.nl);
@@ -310,8 +316,7 @@ __device__ void adjoint_item(const BatchedArgs& a, const DevModel& M, const Work
     } else {                    // recomputed once from the checkpoint
       for (int k = 0; k < M.K; ++k) {
         substep_dynamics(M, w, t.lane, t.nl, nm);
-        float* rec = tape + (size_t)k * REC;
-        for (int j = t.lane; j < REC; j += t.nl) rec[j] = w[j];
+        record_save(tape + (size_t)k * REC, w, REC, t.lane, t.nl);
         team_sync(t.nl);
         st_integrate(M, w, t.lane, t.nl);
       }

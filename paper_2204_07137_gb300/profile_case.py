@@ -27,6 +27,7 @@ def main():
     p.add_argument("--reps", type=int, default=1)
     p.add_argument("--lanes", type=int, default=0)
     p.add_argument("--warps", type=int, default=0)
+    p.add_argument("--tape", type=int, default=1, help="window tape (batched form): 1 keep, 0 recompute")
     a = p.parse_args()
     build.build()
     if a.workload == "hetero":
@@ -37,6 +38,8 @@ def main():
     sim = Simulator(groups, form=a.form, h_max=a.h)
     if a.lanes or a.warps:
         sim.set_launch(-1, a.lanes, a.warps)
+    if a.form == "batched" and a.tape:
+        sim.set_window_tape(True)
     dev = sim.device
     q0 = sim.pack([I.initial_state(m, n, 0)[0] for m, n in groups], "q")
     qd0 = sim.pack([I.initial_state(m, n, 0)[1] for m, n in groups], "qd")

@@ -334,7 +334,10 @@ static int dense_class(int nv, int lanes) {
   return nm <= lanes ? nm : 0;
 }
 
-static int env_stride(const shac_model* m) { return ((m->layout.env_floats + 31) / 32) * 32 + 1; }
+// Shared floats per environment: padded so that every environment's scratch
+// starts 16-byte aligned (records move 16 bytes at a time) and the teams of a
+// warp start 4 banks apart.
+static int env_stride(const shac_model* m) { return ((m->layout.env_floats + 31) / 32) * 32 + 4; }
 
 static size_t batched_smem_warp_floats(const shac_batch* b) {
   size_t per_warp = 0;

@@ -197,11 +197,14 @@ __device__ __forceinline__ void setup_team(const BatchedArgs& a, const WorkItem&
   t.env = it.env0 + (t.active ? t.team : 0);
 }
 
-// Copy a substep record (n floats, a multiple of 4) from scratch to its
-// 16-byte aligned slot in the workspace, 16 bytes per store.
+// Copy a substep record (n floats, a multiple of 4) between an environment's
+// scratch and its slot in the workspace, 16 bytes per access (both sides are
+// 16-byte aligned: the scratch stride and the record length are multiples of 4
+// floats, the dynamic shared memory and the workspace slots 16-byte aligned).
 __device__ __forceinline__ void record_save(float* dst, const SMem& w, int n, int lane, int nl) {
   float4* d4 = reinterpret_cast<float4*>(dst);
-  for (int j = lane; j < n / 4; j += nl) d4[j] = make_float4(w[4 * j], w[4 * j + 1], w[4 * j + 2], w[4 * j + 3]);
+  const float4* s4 = reinterpret_cast<const float4*>(&w[0]);
+  for (int j = lane; j < n / 4; j += nl) d4[j] = s4[j];
 }
 
 // One work item of the forward window (all steps, all substeps).
@@ -271,9 +274,9 @@ __device__ void forward_item(const BatchedArgs& a, const DevModel& M, const Work
 // flight together, then wait for this lane's copies (the caller's team barrier
 // makes them visible to the team).
 __device__ __forceinline__ void record_load(const SMem& w, const float* src, int n, int lane, int nl) {
-  for (int j = lane; j < n; j += nl) {
-    const unsigned dst = (unsigned)__cvta_generic_to_shared(&w[j]);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dst), "l"(src + j) : "memory");
+  for (int j = lane; j < n / 4; j += nl) {
+    const unsigned dst = (unsigned)__cvta_generic_to_shared(&w[4 * j]);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src + 4 * j) : "memory");
   }
   asm volatile("cp.async.commit_group;\n" ::: "memory");
   asm volatile("cp.async.wait_group 0;\n" ::: "memory");
@@ -347,7 +350,7 @@ __device__ void adjoint_item(const BatchedArgs& a, const DevModel& M, const Work
 // capacity of each group is dispatched inside the substep).
 template <bool ADJ>
 __global__ void __maxnreg__(ADJ ? BATCHED_REGS_ADJOINT : BATCHED_REGS_FORWARD) k_batched(BatchedArgs a) {
-  extern __shared__ float smem[];
+  extern __shared__ __align__(16) float smem[];
   __shared__ DevModel s_models[MAX_GROUPS];
   for (int g = threadIdx.x; g < a.n_groups; g += blockDim.x) s_models[g] = a.models[g];
   __syncthreads();

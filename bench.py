@@ -86,6 +86,10 @@ def parse():
                         "N = samples // h environments of the workload's first model (see --samples)")
     p.add_argument("--samples", type=int, default=65536,
                    help="env-steps per window of the --h-sweep study (N x h)")
+    p.add_argument("--shac-episodes", type=int, default=0,
+                   help="time learning episodes of the short-horizon actor-critic learner instead of the contract "
+                        "line (the paper's per-episode forward / backward / critic split)")
+    p.add_argument("--shac-envs", type=int, default=64)
     return p.parse_args()
 
 
@@ -283,6 +287,38 @@ def h_sweep_main(args):
         del sim
     print(json.dumps({"study": "window length h, N x h fixed", "model": model.name, "samples": args.samples,
                       "dtype": "f32", "data": "synthetic", "rows": rows}), flush=True)
+
+
+# ------------------------------------------------------ learner episodes ---
+# The paper's per-learning-episode times (N = 64, h = 32, TITAN X; forward,
+# backward, critic in seconds): context for --shac-episodes, other hardware.
+PAPER_EPISODE_S = {"cartpole": (0.15, 0.23, 0.34), "ant": (0.25, 0.37, 0.32), "humanoid": (0.91, 1.97, 0.32),
+                   "mtu": (0.82, 1.66, 0.33)}
+
+
+def shac_main(args):
+    """Learning episodes of Algorithm 1 on the workload's first model with the
+    paper's N and h: per-episode forward (rollout + policy loss), backward
+    (analytic gradient + actor step) and critic (targets + fit) times, after
+    two warm-up episodes; one JSON line."""
+    import torch
+    from paper_2204_07137_gb300 import build, inputs as I
+    from paper_2204_07137_gb300.shac import SHAC
+
+    build.build()
+    model = I.workload(args.workload).groups[0][0]
+    agent = SHAC(model, n_envs=args.shac_envs, h=H, episodes=args.shac_episodes + 2, seed=0)
+    for _ in range(2):
+        agent.episode()
+    hist = [agent.episode() for _ in range(args.shac_episodes)]
+    mean = {k: float(np.mean([s[k] for s in hist])) for k in ("t_forward", "t_backward", "t_critic")}
+    tot = sum(mean.values())
+    print(json.dumps({"study": "learning episode time (Algorithm 1)", "model": model.name, "n_envs": args.shac_envs,
+                      "h": H, "episodes": args.shac_episodes, "seconds_per_episode": mean, "total_s": tot,
+                      "env_steps_per_s": args.shac_envs * H / tot,
+                      "mean_reward_first_last": [hist[0]["mean_reward"], hist[-1]["mean_reward"]],
+                      "paper_titan_x_s": PAPER_EPISODE_S.get(model.name), "dtype": "f32", "data": "synthetic"}),
+          flush=True)
 
 
 # ------------------------------------------------------------------- GPU ---
@@ -546,6 +582,9 @@ def main():
         elif args.h_sweep:
             if rank == 0:
                 h_sweep_main(args)
+        elif args.shac_episodes > 0:
+            if rank == 0:
+                shac_main(args)
         else:
             gpu_main(args, rank, world, dist)
     finally:

@@ -283,6 +283,20 @@ shac_status shac_batch_get_launch(const shac_batch* batch, int32_t group, int32_
  * Cholesky factor for the backward pass; the tape keeps every intermediate.) */
 shac_status shac_batch_set_window_tape(shac_batch* batch, int32_t keep);
 
+/* Critic value targets of the learner (Sec. 3.2, Eq. td-lambda): for every
+ * environment and t = 0..h-1 the TD-lambda average of the k-step returns
+ * G_t^k = sum_{l<k} gamma^l r_{t+l} + gamma^k V(s_{t+k}) over the window,
+ *   target_t = (1 - lambda) sum_{k=1}^{h-t-1} lambda^{k-1} G_t^k + lambda^{h-t-1} G_t^{h-t}.
+ * Where done_t is set (the episode ended at step t, as written by
+ * shac_window_forward_episodic) the returns of the states up to t stop at step
+ * t with no bootstrap.  Layout [t][n_envs] (environment fastest), device
+ * pointers: reward [h][N], value [h+1][N] (V of the window's states, entry h the
+ * final state), done [h][N] uint8 or NULL (no episode ends), target [h][N]
+ * (written).  Asynchronous on the stream; no allocation.  INVALID_ARG for
+ * null pointers, h < 1, n_envs < 0, gamma or lambda outside [0, 1]. */
+shac_status shac_td_lambda(void* stream, int32_t h, int64_t n_envs, const float* reward, const float* value,
+                           const uint8_t* done, float gamma, float lambda, float* target);
+
 /* Synchronises the stream and returns the sticky device flags
  * (bit 0: non-finite state); clear != 0 resets them.  Not capturable. */
 shac_status shac_get_status(shac_batch* batch, void* stream, uint32_t* sticky_flags, int32_t clear);

@@ -325,3 +325,36 @@ soa = aos
 if __name__ == "__main__":
     build(force="--force" in sys.argv)
     print(_LIB)
+
+
+# ---- learner (Sec. 3.2) -------------------------------------------------------
+
+def td_lambda(reward, value, done, gamma, lam):
+    """Critic targets of Eq. td-lambda, term by term: for each state s_t of the
+    window, the (1 - lambda)-weighted average of its k-step returns
+    G_t^k = sum_{l<k} gamma^l r_{t+l} + gamma^k V(s_{t+k}) plus the weight
+    lambda^(H-1) on the longest one, H the number of steps left in the state's
+    episode inside the window.  An episode that ends at step `end` (done) takes
+    no bootstrap after its last reward; otherwise the window end bootstraps
+    with V(s_h).  reward [h, N], value [h+1, N], done [h, N] or None -> [h, N]."""
+    reward = np.asarray(reward, np.float64)
+    value = np.asarray(value, np.float64)
+    h, N = reward.shape
+    done = np.zeros((h, N), bool) if done is None else np.asarray(done).astype(bool)
+    out = np.zeros((h, N))
+    for e in range(N):
+        for t in range(h):
+            end = t
+            while end < h - 1 and not done[end, e]:
+                end += 1
+            terminal = bool(done[end, e])
+            H = end - t + 1
+
+            def G(k):
+                g = sum(gamma ** l * reward[t + l, e] for l in range(k))
+                if k < H or not terminal:
+                    g += gamma ** k * value[t + k, e]
+                return g
+
+            out[t, e] = (1 - lam) * sum(lam ** (k - 1) * G(k) for k in range(1, H)) + lam ** (H - 1) * G(H)
+    return out

@@ -1,6 +1,6 @@
 """Build libshacsim.so in-tree with nvcc for sm_103a (GB300).
 
-Two translation units compiled in parallel, one -gencode, no cmake.
+Three translation units compiled in parallel, one -gencode, no cmake.
 """
 from __future__ import annotations
 
@@ -13,7 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libshacsim.so")
-SOURCES = ["shac_api.cu", "shac_kernels.cu"]
+SOURCES = ["shac_api.cu", "shac_kernels.cu", "shac_learner.cu"]
 HEADERS = ["shac_device.cuh", "shac_kernels.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]

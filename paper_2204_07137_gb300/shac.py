@@ -1,0 +1,280 @@
+"""Short-horizon actor-critic learner on the GB300 simulator (Sec. 3.2,
+Algorithm 1, appendix A.1 and the hyperparameter tables of the appendix).
+
+One learning episode:
+  1. roll out N trajectories of h steps with the stochastic policy from the end
+     states of the previous episode (Sec. 3.2: gradients are cut between
+     learning episodes), each step through ``SimStep`` (the library's step, its
+     backward the library's step adjoint); an environment whose task ends
+     (root below the task height, or the task horizon) restarts from a fresh
+     seeded initial state, which cuts the gradient there;
+  2. policy loss, Eq. policy_loss: -1/(N h) sum_i [sum_t gamma^(t - t0) r_t +
+     gamma^(h - t0) V_target(s_h)], the discount restarting at every reset;
+  3. one Adam step of the actor on the analytic gradient;
+  4. critic targets by TD-lambda (Eq. td-lambda) with the target critic,
+     computed by the library's ``shac_td_lambda`` kernel;
+  5. critic fit on the window's states (Eq. critic_loss), several iterations
+     over minibatches;
+  6. soft update of the target critic, V' <- alpha V' + (1 - alpha) V;
+  7. running observation normalisation updated with the window's observations.
+
+The networks are ordinary PyTorch modules (dense layers through cuBLAS); the
+simulator, its adjoint and the targets run in the library's kernels.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+from typing import Dict
+
+import numpy as np
+import torch
+from torch import nn
+
+from . import _lib, inputs as I
+from .policy import free_root_observation
+from .sim import SimStep, Simulator
+
+# Appendix hyperparameter tables (optimal settings per task; the general
+# setting for the tasks the tables do not list).
+PAPER_HPARAMS = {
+    "cartpole": dict(actor_lr=1e-2, critic_lr=1e-3, alpha=0.2),
+    "ant": dict(actor_lr=2e-3, critic_lr=2e-3, alpha=0.2),
+    "humanoid": dict(actor_lr=2e-3, critic_lr=5e-4, alpha=0.995),
+    "mtu": dict(actor_lr=2e-3, critic_lr=5e-4, alpha=0.995),
+}
+GENERAL_HPARAMS = dict(actor_lr=2e-3, critic_lr=5e-4, alpha=0.2)
+
+
+def td_lambda(reward: torch.Tensor, value: torch.Tensor, done: torch.Tensor | None, gamma: float,
+              lam: float, stream=None) -> torch.Tensor:
+    """TD-lambda critic targets (Eq. td-lambda) by the library kernel:
+    reward [h, N], value [h+1, N] float32, done [h, N] uint8 or None -> [h, N]."""
+    h, N = reward.shape
+    for name, t, shape in (("reward", reward, (h, N)), ("value", value, (h + 1, N))):
+        if not (t.is_cuda and t.dtype == torch.float32 and t.is_contiguous() and tuple(t.shape) == shape):
+            raise ValueError(f"{name}: expected contiguous float32 CUDA tensor of shape {shape}")
+    if done is not None and not (done.is_cuda and done.dtype == torch.uint8 and done.is_contiguous()
+                                 and tuple(done.shape) == (h, N)):
+        raise ValueError(f"done: expected contiguous uint8 CUDA tensor of shape {(h, N)}")
+    out = torch.empty(h, N, device=reward.device)
+    s = torch.cuda.current_stream(reward.device) if stream is None else stream
+    _lib.check(_lib.load().shac_td_lambda(ctypes.c_void_p(s.cuda_stream), h, N, ctypes.c_void_p(reward.data_ptr()),
+                                          ctypes.c_void_p(value.data_ptr()),
+                                          ctypes.c_void_p(0 if done is None else done.data_ptr()),
+                                          float(gamma), float(lam), ctypes.c_void_p(out.data_ptr())),
+               "shac_td_lambda")
+    return out
+
+
+class RunningNorm:
+    """Running mean and variance of observations (parallel-update form),
+    normalising by the statistics of previous learning episodes."""
+
+    def __init__(self, dim: int, device, eps: float = 1e-5, clip: float = 5.0):
+        self.mean = torch.zeros(dim, dtype=torch.float64, device=device)
+        self.var = torch.ones(dim, dtype=torch.float64, device=device)
+        self.count = eps
+        self.eps = eps
+        self.clip = clip
+
+    def __call__(self, x: torch.Tensor) -> torch.Tensor:
+        y = (x - self.mean.float()) / torch.sqrt(self.var.float() + self.eps)
+        return y.clamp(-self.clip, self.clip)
+
+    def update(self, x: torch.Tensor):
+        x = x.detach().reshape(-1, x.shape[-1]).double()
+        n = x.shape[0]
+        m = x.mean(0)
+        v = x.var(0, unbiased=False)
+        tot = self.count + n
+        d = m - self.mean
+        self.mean = self.mean + d * (n / tot)
+        self.var = (self.var * self.count + v * n + d * d * (self.count * n / tot)) / tot
+        self.count = tot
+
+
+def mlp(sizes, out_scale: float = 1.0):
+    layers = []
+    for k, (a, b) in enumerate(zip(sizes[:-1], sizes[1:])):
+        lin = nn.Linear(a, b)
+        if k == len(sizes) - 2:
+            with torch.no_grad():
+                lin.weight.mul_(out_scale)
+                lin.bias.zero_()
+        layers.append(lin)
+        if k < len(sizes) - 2:
+            layers.append(nn.ELU())
+    return nn.Sequential(*layers)
+
+
+class GaussianPolicy(nn.Module):
+    """a = tanh(mu_theta(o) + sigma_theta * eps), eps ~ N(0, I) given
+    (reparameterisation, Sec. 3.2); sigma a learned per-action scale."""
+
+    def __init__(self, n_obs: int, n_act: int, hidden=(64, 64), log_std0: float = -1.0):
+        super().__init__()
+        self.mu = mlp([n_obs, *hidden, n_act], out_scale=0.1)
+        self.log_std = nn.Parameter(torch.full((n_act,), float(log_std0)))
+
+    def forward(self, obs: torch.Tensor, eps: torch.Tensor) -> torch.Tensor:
+        return torch.tanh(self.mu(obs) + torch.exp(self.log_std) * eps)
+
+
+def observation(model, q: torch.Tensor, qd: torch.Tensor) -> torch.Tensor:
+    """Observation of a single-group state block (q [nq, N], qd [nv, N]) ->
+    [N, n_obs]: free-root models as in the appendix A.3 tables
+    (``policy.free_root_observation``); the cart-pole as in its A.3 table (x,
+    x_dot, sin theta, cos theta, theta_dot); others their coordinates and
+    velocities."""
+    if int(model.joint_type[0]) == I.FREE:
+        return free_root_observation(q, qd)
+    if model.name == "cartpole":
+        return torch.stack([q[0], qd[0], torch.sin(q[1]), torch.cos(q[1]), qd[1]], dim=0).transpose(0, 1)
+    return torch.cat([q, qd], dim=0).transpose(0, 1)
+
+
+class SHAC:
+    """Algorithm 1 on one articulation model with N environments."""
+
+    def __init__(self, model, n_envs: int = 64, h: int = 32, gamma: float = 0.99, lam: float = 0.95,
+                 actor_lr: float | None = None, critic_lr: float | None = None, alpha: float | None = None,
+                 betas=(0.7, 0.95), critic_iters: int = 16, critic_minibatches: int = 4, episodes: int = 500,
+                 seed: int = 0, device=None, grad_clip: float | None = None):
+        hp = dict(PAPER_HPARAMS.get(model.name, GENERAL_HPARAMS))
+        for k, v in (("actor_lr", actor_lr), ("critic_lr", critic_lr), ("alpha", alpha)):
+            if v is not None:
+                hp[k] = v
+        self.model, self.N, self.h, self.gamma, self.lam = model, int(n_envs), int(h), gamma, lam
+        self.alpha, self.critic_iters, self.critic_minibatches = hp["alpha"], critic_iters, critic_minibatches
+        self.episodes = max(1, episodes)
+        self.grad_clip = grad_clip
+        self.sim = Simulator([(model, self.N)], form="batched", h_max=1, device=device)
+        dev = self.sim.device
+        self.device = dev
+        self.term_height, self.horizon = I.episode_rule(model)
+        self.height_q = 2 if int(model.joint_type[0]) == I.FREE else int(model.height_q)
+        g = torch.Generator().manual_seed(seed)
+        torch.manual_seed(seed)
+        self.seed = seed
+        self.n_resets = 0
+        q, qd = self._initial(0)
+        self.q, self.qd = q, qd
+        self.e = torch.from_numpy(np.random.default_rng(seed).integers(0, self.horizon, self.N)).to(dev)
+        n_obs = observation(model, q.view(model.nq, self.N), qd.view(model.nv, self.N)).shape[1]
+        self.actor = GaussianPolicy(n_obs, model.na).to(dev)
+        self.critic = mlp([n_obs, 64, 64, 1]).to(dev)
+        self.target = mlp([n_obs, 64, 64, 1]).to(dev)
+        self.target.load_state_dict(self.critic.state_dict())
+        for p in self.target.parameters():
+            p.requires_grad_(False)
+        self.actor_opt = torch.optim.Adam(self.actor.parameters(), lr=hp["actor_lr"], betas=betas)
+        self.critic_opt = torch.optim.Adam(self.critic.parameters(), lr=hp["critic_lr"], betas=betas)
+        self.lr0 = (hp["actor_lr"], hp["critic_lr"])
+        self.norm = RunningNorm(n_obs, dev)
+        self.rng = torch.Generator(device=dev).manual_seed(seed + 1)
+        self.episode_index = 0
+
+    def _initial(self, k: int):
+        q, qd = I.initial_state(self.model, self.N, self.seed * 1000 + k)
+        return (torch.from_numpy(q.reshape(-1)).to(self.device), torch.from_numpy(qd.reshape(-1)).to(self.device))
+
+    def _obs(self, q, qd):
+        return observation(self.model, q.view(self.model.nq, self.N), qd.view(self.model.nv, self.N))
+
+    @torch.no_grad()
+    def evaluate(self, steps: int, seed: int) -> float:
+        """Mean reward of the deterministic policy (eps = 0) over `steps` steps
+        from fresh seeded initial states (a separate batch; no learning)."""
+        m, N = self.model, self.N
+        q, qd = (torch.from_numpy(x.reshape(-1)).to(self.device) for x in I.initial_state(m, N, 10_000 + seed))
+        zero = torch.zeros(N, m.na, device=self.device)
+        tot = 0.0
+        for _ in range(steps):
+            a = self.actor(self.norm(self._obs(q, qd)), zero)
+            q, qd, r = self.sim.step(q, qd, a.transpose(0, 1).contiguous().view(-1))
+            tot += float(r.mean())
+        return tot / steps
+
+    def episode(self) -> Dict[str, float]:
+        """One learning episode; returns its losses, mean reward and the
+        forward / backward / critic times in seconds (CUDA events)."""
+        m, N, h, gamma = self.model, self.N, self.h, self.gamma
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        frac = 1.0 - self.episode_index / self.episodes          # linear learning-rate decay
+        for opt, lr0 in ((self.actor_opt, self.lr0[0]), (self.critic_opt, self.lr0[1])):
+            for grp in opt.param_groups:
+                grp["lr"] = lr0 * max(frac, 0.0)
+        ev[0].record()
+        # 1-2. rollout through the differentiable simulator and the policy loss
+        q, qd = self.q, self.qd                                  # detached: cut between episodes
+        q_reset, qd_reset = self._initial(1 + self.episode_index)
+        disc = torch.ones(N, device=self.device)
+        total = torch.zeros(N, device=self.device)
+        obs_raw, rews, dones = [], [], []
+        for t in range(h):
+            o = self._obs(q, qd)
+            obs_raw.append(o.detach())
+            eps = torch.randn(N, m.na, device=self.device, generator=self.rng)
+            a = self.actor(self.norm(o), eps)
+            qn, qdn, r = SimStep.apply(self.sim, q, qd, a.transpose(0, 1).contiguous().view(-1))
+            total = total + disc * r
+            self.e = self.e + 1
+            d = self.e >= self.horizon
+            if self.height_q >= 0 and self.term_height > -math.inf:
+                d = d | (qn.view(m.nq, N)[self.height_q] < self.term_height)
+            self.e = torch.where(d, torch.zeros_like(self.e), self.e)
+            disc = torch.where(d, torch.ones_like(disc), disc * gamma)
+            # an ended episode restarts from a reset state: a constant, so no gradient crosses it
+            dq = d.repeat(m.nq)
+            dqd = d.repeat(m.nv)
+            q = torch.where(dq, q_reset, qn)
+            qd = torch.where(dqd, qd_reset, qdn)
+            rews.append(r.detach())
+            dones.append(d)
+        o_end = self._obs(q, qd)
+        obs_raw.append(o_end.detach())
+        v_end = self.target(self.norm(o_end)).squeeze(-1)
+        total = total + disc * v_end
+        loss = -total.sum() / (N * h)
+        ev[1].record()
+        # 3. actor update on the analytic gradient
+        self.actor_opt.zero_grad(set_to_none=True)
+        loss.backward()
+        if self.grad_clip is not None:
+            nn.utils.clip_grad_norm_(self.actor.parameters(), self.grad_clip)
+        self.actor_opt.step()
+        self.q, self.qd = q.detach(), qd.detach()
+        ev[2].record()
+        # 4-6. critic: TD-lambda targets with the target critic, fit, soft update
+        with torch.no_grad():
+            obs_all = torch.stack(obs_raw)                       # [h+1, N, n_obs]
+            on = self.norm(obs_all)
+            values = self.target(on).squeeze(-1).contiguous()   # [h+1, N]
+            reward = torch.stack(rews).contiguous()
+            done = torch.stack(dones).to(torch.uint8).contiguous()
+            tgt = td_lambda(reward, values, done, gamma, self.lam)
+        x = on[:h].reshape(h * N, -1)
+        y = tgt.reshape(h * N)
+        c_loss = 0.0
+        for _ in range(self.critic_iters):
+            perm = torch.randperm(h * N, device=self.device, generator=self.rng)
+            for b in perm.chunk(self.critic_minibatches):
+                pred = self.critic(x[b]).squeeze(-1)
+                l = ((pred - y[b]) ** 2).mean()
+                self.critic_opt.zero_grad(set_to_none=True)
+                l.backward()
+                self.critic_opt.step()
+                c_loss = float(l.detach())
+        with torch.no_grad():
+            for pt, pc in zip(self.target.parameters(), self.critic.parameters()):
+                pt.mul_(self.alpha).add_(pc, alpha=1.0 - self.alpha)
+        # 7. observation statistics of this episode, used from the next one on
+        self.norm.update(obs_all[:h])
+        ev[3].record()
+        torch.cuda.synchronize()
+        self.episode_index += 1
+        return {"policy_loss": float(loss.detach()), "critic_loss": c_loss,
+                "mean_reward": float(reward.mean()), "resets": int(done.sum()),
+                "t_forward": ev[0].elapsed_time(ev[1]) * 1e-3, "t_backward": ev[1].elapsed_time(ev[2]) * 1e-3,
+                "t_critic": ev[2].elapsed_time(ev[3]) * 1e-3}

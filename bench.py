@@ -232,8 +232,8 @@ def h_sweep_main(args):
     """Window-length study (the paper's horizon study: every variant draws
     the same number of samples per learning episode, N x h fixed): for each
     h, N = samples // h environments run the graph-captured forward + adjoint
-    window; one JSON line with env-steps/s, ms per window and the kernel split
-    per h.  L2 flushed before each timed window."""
+    window (window tape kept); one JSON line with env-steps/s, ms per window and
+    the kernel split per h.  L2 flushed before each timed window."""
     import torch
     from paper_2204_07137_gb300 import build, inputs as I
     from paper_2204_07137_gb300.sim import Simulator
@@ -247,6 +247,7 @@ def h_sweep_main(args):
     for h in [int(x) for x in args.h_sweep.split(",")]:
         N = max(1, args.samples // h)
         sim = Simulator([(model, N)], form="batched", h_max=h)
+        sim.set_window_tape(True)
         q0, qd0 = (torch.from_numpy(np.ascontiguousarray(x.reshape(-1))).to(dev) for x in I.initial_state(model, N, 0))
         act = torch.from_numpy(I.window_actions(model, N, h, 0).reshape(h, -1)).to(dev).contiguous()
         rbar = torch.full((h, N), 1.0 / (N * h), device=dev)

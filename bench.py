@@ -57,10 +57,11 @@ ALGO_FLOPS_PER_ENV_STEP = {
     "ant-2048": {"forward": 134692, "adjoint": 172338},
 }
 
-# DRAM traffic (read + write) per launch of each batched kernel at h = 32 on
-# ant-2048, scaled from an ncu capture at h = 2 by the 16x env-steps (the
-# per-step traffic is the same at every step); profiles/batched_ant_2048.md.
-TRAFFIC_BYTES_PER_LAUNCH = {}   # re-taken on the window-tape kernels below
+# DRAM traffic (read + write) of one launch of each batched kernel on the full
+# 32-step ant-2048 window with the window tape (one-pass ncu capture of that
+# launch); profiles/batched_ant_2048.md.
+TRAFFIC_BYTES_PER_LAUNCH = {"ant-2048": {"k_batched_forward": 8.31e6 + 2.81e9,
+                                         "k_batched_adjoint": 2.88e9 + 2.54e6}}
 
 # Algorithmic HBM bytes per env-step (ant): forward reads the action (8 f32)
 # and writes the checkpoint (29) and reward (1); the adjoint reads checkpoint

@@ -335,15 +335,17 @@ static int dense_class(int nv, int lanes) {
 }
 
 // Shared floats per environment: padded so that every environment's scratch
-// starts 16-byte aligned (records move 16 bytes at a time) and the teams of a
-// warp start 4 banks apart.
-static int env_stride(const shac_model* m) { return ((m->layout.env_floats + 31) / 32) * 32 + 4; }
+// starts 16-byte aligned (records move 16 bytes at a time) and the 32 / lanes
+// teams of a warp start spread over the 32 banks (lanes apart, at least 4).
+static int env_stride(const shac_model* m, int lanes) {
+  return ((m->layout.env_floats + 31) / 32) * 32 + (lanes >= 4 ? lanes % 32 : 4);
+}
 
 static size_t batched_smem_warp_floats(const shac_batch* b) {
   size_t per_warp = 0;
   for (const Group& g : b->groups) {
     if (g.N == 0) continue;
-    per_warp = std::max(per_warp, (size_t)(32 / g.lanes) * env_stride(g.m));
+    per_warp = std::max(per_warp, (size_t)(32 / g.lanes) * env_stride(g.m, g.lanes));
   }
   return per_warp;
 }
@@ -535,7 +537,7 @@ static shac_status batched_launch(shac_batch* b, BatchedArgs& a, void* ws, cudaS
   a.io = b->io;
   for (int gi = 0; gi < a.n_groups; ++gi) {
     a.lanes[gi] = b->groups[gi].lanes;
-    a.env_stride[gi] = env_stride(b->groups[gi].m);
+    a.env_stride[gi] = env_stride(b->groups[gi].m, b->groups[gi].lanes);
     a.dense_nm[gi] = dense_class(b->groups[gi].m->nv, b->groups[gi].lanes);
   }
   a.smem_warp_floats = (int)batched_smem_warp_floats(b);

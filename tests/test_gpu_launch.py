@@ -53,3 +53,25 @@ def test_every_cta_size_launches_in_a_fresh_context():
     out = subprocess.run([sys.executable, "-c", CHILD, ROOT], capture_output=True, text=True, timeout=600)
     assert out.returncode == 0, out.stdout[-2000:] + out.stderr[-4000:]
     assert out.stdout.strip().endswith("ok")
+
+
+def test_autotune_picks_a_valid_shape():
+    """The launch-shape tuner measures candidate team sizes and CTA sizes on a
+    heterogeneous batch, leaves the batch on a valid shape, and that shape
+    gives the same window up to FP32 reassociation inside a team."""
+    import numpy as np
+    from paper_2204_07137_gb300 import autotune, inputs as I
+    from paper_2204_07137_gb300.sim import Simulator
+    groups = [(I.cartpole(), 40), (I.ant(), 13)]
+    tuned = Simulator(groups, form="batched", h_max=2)
+    ref = Simulator(groups, form="batched", h_max=2)
+    r = autotune.autotune(tuned, h=2, reps=1)
+    assert all(l in autotune.LANES for l in r["lanes"]) and r["warps"] in autotune.WARPS
+    assert np.isfinite(r["ms_window_h"])
+    assert [tuned.get_launch(g)[0] for g in range(2)] == r["lanes"]
+    x = autotune._Inputs(ref, 2)
+    a = tuned.window_forward(x.q0, x.qd0, x.act)
+    b = ref.window_forward(x.q0, x.qd0, x.act)
+    torch.cuda.synchronize()
+    for u, v in zip(a, b):
+        np.testing.assert_allclose(u.cpu().numpy(), v.cpu().numpy(), rtol=1e-4, atol=1e-3)

@@ -154,10 +154,8 @@ class SHAC:
         self.device = dev
         self.term_height, self.horizon = I.episode_rule(model)
         self.height_q = 2 if int(model.joint_type[0]) == I.FREE else int(model.height_q)
-        g = torch.Generator().manual_seed(seed)
-        torch.manual_seed(seed)
+        torch.manual_seed(seed)   # network initialisation
         self.seed = seed
-        self.n_resets = 0
         q, qd = self._initial(0)
         self.q, self.qd = q, qd
         self.e = torch.from_numpy(np.random.default_rng(seed).integers(0, self.horizon, self.N)).to(dev)

@@ -4,7 +4,7 @@ execution forms; sizes span several work items with a ragged tail."""
 import numpy as np
 import pytest
 
-from helpers import (GRAD_RTOL, airborne, assert_grad_close, assert_state_close, model_by_name,
+from helpers import (airborne, assert_grad_close, assert_state_close, model_by_name,
                      seeded_case)
 from paper_2204_07137_gb300 import inputs as I
 

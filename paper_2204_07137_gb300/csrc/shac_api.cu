@@ -325,13 +325,15 @@ static int default_lanes(const shac_model* m) {
   return 32;
 }
 
-// Register row capacity of the batched dense path (2, 4, 8, 12, ..., 32: the
-// device instantiations): a team needs one lane per padded row; 0 selects the
-// shared-memory form.
+// Register row capacity of the batched dense path: the smallest of the device
+// instantiations (2, 4, 6, 8, 10, 12, 14, 16, 20, 24, 28, 32 rows) that holds
+// nv rows, one padded row per lane, when the team has that many lanes; 0
+// selects the shared-memory form.
 static int dense_class(int nv, int lanes) {
-  if (lanes < 2 || lanes < nv || nv > 32) return 0;
-  const int nm = nv <= 2 ? 2 : nv <= 4 ? 4 : ((nv + 3) / 4) * 4;
-  return nm <= lanes ? nm : 0;
+  static const int sizes[] = {2, 4, 6, 8, 10, 12, 14, 16, 20, 24, 28, 32};
+  for (int nm : sizes)
+    if (nm >= nv) return nm <= lanes ? nm : 0;
+  return 0;
 }
 
 // Shared floats per environment: padded so that every environment's scratch

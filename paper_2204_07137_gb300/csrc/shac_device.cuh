@@ -836,7 +836,7 @@ __device__ __forceinline__ void dense_stored_solve(const DevModel& M, const Mem&
 }
 
 // Row capacities of the register path (see dense_class on the host).
-#define SHAC_DENSE_CASES(X) X(2) X(4) X(8) X(12) X(16) X(20) X(24) X(28) X(32)
+#define SHAC_DENSE_CASES(X) X(2) X(4) X(6) X(8) X(10) X(12) X(14) X(16) X(20) X(24) X(28) X(32)
 
 template <class Mem>
 __device__ __forceinline__ void dense_substep_nm(const DevModel& M, const Mem& w, int lane, int nl, int nm, float b) {

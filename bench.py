@@ -71,6 +71,16 @@ TRAFFIC_BYTES_PER_LAUNCH = {"ant-2048": {"k_batched_forward": 8.31e6 + 2.81e9,
 ALGO_BYTES_PER_ENV_STEP = {"k_batched_forward": 4 * (8 + 29 + 1), "k_batched_adjoint": 4 * (29 + 8 + 1 + 8)}
 
 
+def measured_hbm_gbs():
+    """Measured HBM copy bandwidth of this machine's GPUs (MEASURED_PEAKS.json,
+    written next to this file by the harness), else the fallback figure."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "fallback 6.8 TB/s"
+
+
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
@@ -500,6 +510,10 @@ def gpu_main(args, rank, world, dist):
     af = counts["adjoint" if dominant.endswith("adjoint") else "forward"] if counts else None
     achieved = None if af is None else af * n_envs * H / (ms_dom * 1e-3) / 1e12
     traffic = TRAFFIC_BYTES_PER_LAUNCH.get(wl.name, {}).get(dominant)
+    hbm_peak, hbm_src = measured_hbm_gbs()
+    hbm_bytes = traffic if traffic is not None else \
+        (ALGO_BYTES_PER_ENV_STEP.get(dominant, 0) + tape_bytes) * n_envs * H
+    hbm_gbs = hbm_bytes / (ms_dom * 1e-3) / 1e9
     line = {
         "metric": METRIC, "value": value, "unit": "env-steps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_batched, "higher_is_better": True, "scaling": "weak",
@@ -531,14 +545,34 @@ def gpu_main(args, rank, world, dist):
                      "unit": "TFLOP/s", "frac": None if achieved is None else achieved / FP32_PEAK_TFLOPS,
                      "peak_source": "derived FP32 peak: 152 SMs x 128 lanes x 2 x 2.07 GHz",
                      "traffic": traffic, "algo_flops_per_env_step": af,
-                     "algo_bytes_per_env_step": ALGO_BYTES_PER_ENV_STEP.get(dominant, 0) + tape_bytes},
+                     "algo_bytes_per_env_step": ALGO_BYTES_PER_ENV_STEP.get(dominant, 0) + tape_bytes,
+                     "hbm": {"achieved": hbm_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": hbm_gbs / hbm_peak,
+                             "bytes": "ncu traffic" if traffic is not None else "algorithmic",
+                             "peak_source": hbm_src}},
     }
     if not args.no_cpu_baseline:
         r, n, hs, threads, dt = oracle_window_rate(groups[0][0], groups[0][1], seed=0, target_s=12.0)
         line["cpu_baseline"] = {"value": r, "unit": "env-steps/s", "cores": threads, "kind": "oracle",
                                 "sample": f"{n} of {groups[0][1]} envs ({groups[0][0].name}) x {hs} steps, "
-                                          f"forward + exact adjoint, {dt:.1f} s"}
+                                          f"forward + exact adjoint, {dt:.1f} s",
+                                "single_core": oracle_single_core_rate(args.workload)}
     print(json.dumps(line), flush=True)
+
+
+def oracle_single_core_rate(workload: str):
+    """The oracle's env-steps/s on one host core (a child process with one
+    OpenMP thread, a bounded sample of about 4 s); None if it fails."""
+    code = ("import json, sys; sys.path.insert(0, sys.argv[1]); import bench; "
+            "from paper_2204_07137_gb300 import inputs as I; m, N = I.workload(sys.argv[2]).groups[0]; "
+            "r, n, hs, t, dt = bench.oracle_window_rate(m, N, seed=0, target_s=4.0); "
+            "print(json.dumps({'value': r, 'unit': 'env-steps/s', 'cores': t, "
+            "'sample': f'{n} envs x {hs} steps, {dt:.1f} s'}))")
+    try:
+        out = subprocess.run([sys.executable, "-c", code, ROOT, workload], capture_output=True, text=True,
+                             timeout=300, env={**os.environ, "OMP_NUM_THREADS": "1"})
+        return json.loads(out.stdout.strip().splitlines()[-1])
+    except (subprocess.SubprocessError, ValueError, IndexError):
+        return None
 
 
 def gradient_check(sim, groups, outf, outa, act, rbar, n_sample: int = 4):

@@ -60,8 +60,8 @@ ALGO_FLOPS_PER_ENV_STEP = {
 # DRAM traffic (read + write) of one launch of each batched kernel on the full
 # 32-step ant-2048 window with the window tape (one-pass ncu capture of that
 # launch); profiles/batched_ant_2048.md.
-TRAFFIC_BYTES_PER_LAUNCH = {"ant-2048": {"k_batched_forward": 8.31e6 + 2.81e9,
-                                         "k_batched_adjoint": 2.88e9 + 2.54e6}}
+TRAFFIC_BYTES_PER_LAUNCH = {"ant-2048": {"k_batched_forward": 8.36e6 + 2.81e9,
+                                         "k_batched_adjoint": 2.89e9 + 3.16e6}}
 
 # Algorithmic HBM bytes per env-step (ant): forward reads the action (8 f32)
 # and writes the checkpoint (29) and reward (1); the adjoint reads checkpoint
@@ -191,30 +191,47 @@ def oracle_window_rate(model, n_envs: int, seed: int = 0, target_s: float = 12.0
     return n * hs / dt, n, hs, threads, dt
 
 
+def oracle_workload_rate(groups, seed: int = 0, target_s: float = 12.0):
+    """env-steps/s of the oracle on a whole workload: each articulation group
+    sampled on its own (target_s split by group), combined as the whole job's
+    env-steps over the sum of the groups' times, sum N_g / sum (N_g / r_g).
+    Returns (rate, threads, seconds sampled, sample description)."""
+    per = target_s / len(groups)
+    total_n, total_t, dts, parts, threads = 0, 0.0, 0.0, [], 1
+    for model, n_g in groups:
+        r, n, hs, threads, dt = oracle_window_rate(model, n_g, seed=seed, target_s=per)
+        total_n += n_g
+        total_t += n_g / r
+        dts += dt
+        parts.append(f"{n} of {n_g} envs ({model.name}) x {hs} steps")
+    return total_n / total_t, threads, dts, "; ".join(parts)
+
+
 def reference_main(args, rank, world):
     from paper_2204_07137_gb300 import inputs as I
     if rank != 0:
         return
     wl = I.workload(args.workload)
-    model, n_total = wl.groups[0]
+    n_total = sum(n for _, n in wl.groups)
     rates = []
     for _ in range(args.warmup):
         pass   # the oracle has no warm-up state; W untimed steps are not needed on the CPU
     samples = []
     for s in range(args.steps):
-        r, n, hs, threads, dt = oracle_window_rate(model, n_total, seed=s,
-                                                   target_s=min(12.0, 60.0 / max(1, args.steps)))
+        r, threads, dt, desc = oracle_workload_rate(wl.groups, seed=s, target_s=min(12.0, 60.0 / max(1, args.steps)))
         rates.append(r)
-        samples.append((n, hs, dt))
+        samples.append(desc)
     value = statistics.median(rates)
+    model = wl.groups[0][0]
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "env-steps/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * n_total * H / value,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": wl.name, "n_envs": n_total, "h": H, "substeps": model.substeps,
+        "config": {"workload": wl.name, "n_envs": n_total, "h": H,
+                   "substeps": model.substeps if len(wl.groups) == 1 else [m.substeps for m, _ in wl.groups],
                    "form": "FP64 CPU oracle, forward + dual-number exact adjoint"},
         "cpu_baseline": {"value": value, "unit": "env-steps/s", "cores": threads, "kind": "oracle",
-                         "sample": f"{samples[0][0]} of {n_total} envs x {samples[0][1]} steps per timed step"},
+                         "sample": f"{samples[0]} per timed step"},
         "e2e": {"value": value, "unit": "env-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -519,7 +536,7 @@ def gpu_main(args, rank, world, dist):
         "warmup": args.warmup, "ms_per_step": ms_batched, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": wl.name, "n_envs_per_gpu": n_envs, "h": H,
-                   "substeps": groups[0][0].substeps,
+                   "substeps": groups[0][0].substeps if len(groups) == 1 else [m.substeps for m, _ in groups],
                    "form": "batched, forward+adjoint captured in one CUDA graph, window tape kept in HBM",
                    "tape_bytes_per_env_step": tape_bytes,
                    "lanes_per_env": [sim.get_launch(g)[0] for g in range(len(groups))],
@@ -551,10 +568,9 @@ def gpu_main(args, rank, world, dist):
                              "peak_source": hbm_src}},
     }
     if not args.no_cpu_baseline:
-        r, n, hs, threads, dt = oracle_window_rate(groups[0][0], groups[0][1], seed=0, target_s=12.0)
+        r, threads, dt, desc = oracle_workload_rate(groups, seed=0, target_s=12.0)
         line["cpu_baseline"] = {"value": r, "unit": "env-steps/s", "cores": threads, "kind": "oracle",
-                                "sample": f"{n} of {groups[0][1]} envs ({groups[0][0].name}) x {hs} steps, "
-                                          f"forward + exact adjoint, {dt:.1f} s",
+                                "sample": f"{desc}, forward + exact adjoint, {dt:.1f} s",
                                 "single_core": oracle_single_core_rate(args.workload)}
     print(json.dumps(line), flush=True)
 
@@ -563,10 +579,10 @@ def oracle_single_core_rate(workload: str):
     """The oracle's env-steps/s on one host core (a child process with one
     OpenMP thread, a bounded sample of about 4 s); None if it fails."""
     code = ("import json, sys; sys.path.insert(0, sys.argv[1]); import bench; "
-            "from paper_2204_07137_gb300 import inputs as I; m, N = I.workload(sys.argv[2]).groups[0]; "
-            "r, n, hs, t, dt = bench.oracle_window_rate(m, N, seed=0, target_s=4.0); "
+            "from paper_2204_07137_gb300 import inputs as I; "
+            "r, t, dt, desc = bench.oracle_workload_rate(I.workload(sys.argv[2]).groups, seed=0, target_s=4.0); "
             "print(json.dumps({'value': r, 'unit': 'env-steps/s', 'cores': t, "
-            "'sample': f'{n} envs x {hs} steps, {dt:.1f} s'}))")
+            "'sample': f'{desc}, {dt:.1f} s'}))")
     try:
         out = subprocess.run([sys.executable, "-c", code, ROOT, workload], capture_output=True, text=True,
                              timeout=300, env={**os.environ, "OMP_NUM_THREADS": "1"})

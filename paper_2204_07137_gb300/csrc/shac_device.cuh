@@ -329,6 +329,13 @@ __device__ __forceinline__ void lk_kin(const DevModel& M, const Mem& w, int i, K
   const V3 ax = cld3(M.axis + 3 * i);
   const M33 Rl = ldm(w, M.o_R + 9 * i);
   const V3 Pl = ld3(w, M.o_P + 3 * i);
+  float qdv[6];
+  if (jt == J_FREE) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) qdv[k] = w[M.o_QD + d0 + k];
+  } else {
+    qdv[0] = nd == 1 ? w[M.o_QD + d0] : 0.f;
+  }
   M33 R;
   V3 P;
   if (jt == J_FREE || p < 0) {
@@ -344,7 +351,7 @@ __device__ __forceinline__ void lk_kin(const DevModel& M, const Mem& w, int i, K
   auto subspace = [&](int k, V3 sw, V3 sv) {
     st3(w, M.o_S + 6 * (d0 + k), sw);
     st3(w, M.o_S + 6 * (d0 + k) + 3, sv);
-    const float qd = w[M.o_QD + d0 + k];
+    const float qd = qdv[k];
     uw = uw + qd * sw;
     uv = uv + qd * sv;
   };
@@ -862,7 +869,7 @@ __device__ __forceinline__ void dense_stored_solve_nm(const DevModel& M, const M
 // nm = 0: shared-memory dense stages (any team size, incl. one thread per
 // environment); nm > 0: register-resident dense path of that row capacity.
 template <class Mem>
-__device__ void substep_dynamics(const DevModel& M, const Mem& w, int lane, int nl, int nm) {
+__device__ __forceinline__ void substep_dynamics(const DevModel& M, const Mem& w, int lane, int nl, int nm) {
   sw_forward(M, w, lane, nl);
   sw_gather(M, w, lane, nl);
   if (nm > 0) {
@@ -1263,14 +1270,27 @@ __device__ __forceinline__ void lk_adj_bwd(const DevModel& M, const Mem& w, int 
     for (int t = 0; t < 9; ++t) Rb.m[t] += g.tR.m[t];
     Pb = Pb + g.tP;
   }
+  // the rest of link i's scratch reads come before its first store
+  V3 uw, uv;
+  joint_vel(M, w, i, uw, uv);
+  const V3 Vw = ld3(w, M.o_V + 6 * i), Vv = ld3(w, M.o_V + 6 * i + 3);
+  const M33 R = ldm(w, M.o_R + 9 * i);
+  const V3 P = ld3(w, M.o_P + 3 * i);
+  const int jt = __ldg(M.jtype + i), d0 = __ldg(M.ds + i), nd = __ldg(M.nd + i);
+  const int p = __ldg(M.parent + i);
+  M33 Rloc;   // joint-local rotation kept in o_TP by lk_adj_local (revolute with a parent)
+  if (jt == J_REV && p >= 0) Rloc = ldm(w, M.o_TP + 12 * i);
+  float lam1 = 0.f, qdd1 = 0.f, qd1 = 0.f, qdb1 = 0.f;   // a one-DOF joint's terms
+  V3 s1w = v3(0.f, 0.f, 0.f), s1v = v3(0.f, 0.f, 0.f);
+  if (jt != J_FREE && nd == 1) {
+    lam1 = w[M.o_LAM + d0]; qdd1 = w[M.o_QDD + d0]; qd1 = w[M.o_QD + d0]; qdb1 = w[M.o_QDB + d0];
+    s1w = ld3(w, M.o_S + 6 * d0); s1v = ld3(w, M.o_S + 6 * d0 + 3);
+  }
   st3(w, M.o_F + 6 * i, Fn);
   st3(w, M.o_F + 6 * i + 3, Ff);
   st3(w, M.o_AB + 6 * i, an);
   st3(w, M.o_AB + 6 * i + 3, af);
   // A_i = A_p + sum S qdd + V_i x u_i
-  V3 uw, uv;
-  joint_vel(M, w, i, uw, uv);
-  const V3 Vw = ld3(w, M.o_V + 6 * i), Vv = ld3(w, M.o_V + 6 * i + 3);
   vw = vw + cross(uw, an) + cross(uv, af) + cvw;
   vv = vv + cross(uw, af) + cvv;
   st3(w, M.o_VB + 6 * i, vw);
@@ -1278,9 +1298,6 @@ __device__ __forceinline__ void lk_adj_bwd(const DevModel& M, const Mem& w, int 
   const V3 ubw = cross(an, Vw) + cross(af, Vv);
   const V3 ubv = cross(af, Vw);
   // motion subspaces of the DOFs of i: tau = S^T F_total, A and V terms
-  const M33 R = ldm(w, M.o_R + 9 * i);
-  const V3 P = ld3(w, M.o_P + 3 * i);
-  const int jt = __ldg(M.jtype + i), d0 = __ldg(M.ds + i), nd = __ldg(M.nd + i);
   const V3 ax = cld3(M.axis + 3 * i);
   // per DOF: tau = S^T F_total gives qd_bar and the subspace cotangents
   // (sbw, sbv); DOF counts are fixed by the joint type, so the column index
@@ -1309,8 +1326,10 @@ __device__ __forceinline__ void lk_adj_bwd(const DevModel& M, const Mem& w, int 
       Rb.m[k] += sbv.x; Rb.m[3 + k] += sbv.y; Rb.m[6 + k] += sbv.z;
     }
   } else if (nd == 1) {
-    V3 sbw, sbv;
-    dof_terms(0, sbw, sbv);
+    const float wd = -lam1;
+    w[M.o_QDB + d0] = qdb1 + (dot(s1w, ubw + vw) + dot(s1v, ubv + vv));
+    const V3 sbw = wd * Fn + qdd1 * an + qd1 * (ubw + vw);
+    const V3 sbv = wd * Ff + qdd1 * af + qd1 * (ubv + vv);
     V3 ab;
     if (jt == J_REV) {   // (a, P x a), a = R ax
       const V3 a = mul(R, ax);
@@ -1324,12 +1343,11 @@ __device__ __forceinline__ void lk_adj_bwd(const DevModel& M, const Mem& w, int 
   stm(w, M.o_RB + 9 * i, Rb);
   st3(w, M.o_PB + 3 * i, Pb);
   g.Fn = Fn; g.Ff = Ff; g.an = an; g.af = af; g.vw = vw; g.vv = vv;
-  const int p = __ldg(M.parent + i);
   if (p >= 0 && jt != J_FREE) {
     // Rj = Rp jrot (joint frame in world), R = Rj Rot(ax, q), Pj = Pp + Rp jpos
     M33 tp;
     if (jt == J_REV) {
-      tp = mulBT(Rb, ldm(w, M.o_TP + 12 * i));   // R_p_bar = R_bar R_local^T
+      tp = mulBT(Rb, Rloc);   // R_p_bar = R_bar R_local^T
     } else {
       M33 Rjb = Rb;
       if (jt == J_PRIS) add_outer(Rjb, w[M.o_Q + __ldg(M.qs + i)] * Pb, ax);   // P = Pj + q Rj ax
@@ -1380,7 +1398,7 @@ __device__ __forceinline__ void lk_adj_qbar(const DevModel& M, const Mem& w, int
 // substep (o_QDD holds the solved accelerations, o_M/o_LD the factor), add
 // -lambda^T dG/d(q, qd, a) to o_QB, o_QDB, o_ACTB with lambda = M^{-1} qdd_bar.
 template <class Mem>
-__device__ void st_dynamics_adj(const DevModel& M, const Mem& w, int lane, int nl, int nm) {
+__device__ __forceinline__ void st_dynamics_adj(const DevModel& M, const Mem& w, int lane, int nl, int nm) {
   if (nm > 0) {
     dense_stored_solve_nm(M, w, lane, nl, nm, M.o_T, M.o_LAM);
   } else {

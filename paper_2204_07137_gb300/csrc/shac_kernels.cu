@@ -208,7 +208,7 @@ __device__ __forceinline__ void record_save(float* dst, const SMem& w, int n, in
 }
 
 // One work item of the forward window (all steps, all substeps).
-__device__ void forward_item(const BatchedArgs& a, const DevModel& M, const WorkItem& it, const SMem& w,
+__device__ __forceinline__ void forward_item(const BatchedArgs& a, const DevModel& M, const WorkItem& it, const SMem& w,
                              const Team& t) {
   const int nm = a.dense_nm[it.group];
   const GroupIO& io = a.io.g[it.group];
@@ -288,7 +288,7 @@ __device__ __forceinline__ void record_load(const SMem& w, const float* src, int
 // the workspace and reloaded by the reverse pass.  With the window tape the
 // forward window already kept every record (and the post-step state), and the
 // recompute is skipped.
-__device__ void adjoint_item(const BatchedArgs& a, const DevModel& M, const WorkItem& it, const SMem& w,
+__device__ __forceinline__ void adjoint_item(const BatchedArgs& a, const DevModel& M, const WorkItem& it, const SMem& w,
                              const Team& t) {
   const int nm = a.dense_nm[it.group];
   const GroupIO& io = a.io.g[it.group];
@@ -347,7 +347,13 @@ __device__ void adjoint_item(const BatchedArgs& a, const DevModel& M, const Work
 }
 
 // Persistent kernels: warps pull work items (the dense path's register
-// capacity of each group is dispatched inside the substep).
+// capacity of each group is dispatched inside the substep).  Everything a
+// kernel runs is inlined into it (forward_item, adjoint_item, the substep
+// and its adjoint are forced inline): inside one body the compiler sees that
+// the scratch (dynamic shared memory) and the model table (s_models) are
+// different arrays, so model fields are not reloaded after every scratch
+// store, and no call boundary splits the register allocation (measured on
+// the ant-like 2048-environment window: forward 5.99 -> 5.36 ms).
 template <bool ADJ>
 __global__ void __maxnreg__(ADJ ? BATCHED_REGS_ADJOINT : BATCHED_REGS_FORWARD) k_batched(BatchedArgs a) {
   extern __shared__ __align__(16) float smem[];

@@ -162,9 +162,11 @@ class ClockSampler:
 # --------------------------------------------------------------- reference --
 def oracle_window_rate(model, n_envs: int, seed: int = 0, target_s: float = 12.0):
     """env-steps/s of the FP64 oracle (window forward + exact adjoint) on a
-    bounded sample of the workload: hs steps of n environments, grown (steps
-    first, up to the 32-step window, then environments) until the sample takes
-    about target_s / 4 .. target_s of wall time."""
+    bounded sample of the workload: hs steps of n environments, starting from
+    one environment per oracle thread (the oracle runs environments in
+    parallel) and grown (steps first, up to the 32-step window, then
+    environments) until the sample takes about target_s / 4 .. target_s of
+    wall time."""
     from paper_2204_07137_gb300 import inputs as I
     from oracle import oracle
     o = oracle.Oracle(model)
@@ -179,7 +181,7 @@ def oracle_window_rate(model, n_envs: int, seed: int = 0, target_s: float = 12.0
         return time.perf_counter() - t0
 
     threads = oracle.num_threads()
-    n, hs = 1, 1
+    n, hs = max(1, min(threads, n_envs)), 1
     dt = run(n, hs)
     while dt < target_s / 4 and (hs < H or n < n_envs):
         grow = min(8.0, target_s / max(dt, 1e-3))

@@ -1062,20 +1062,25 @@ __device__ __forceinline__ void si_adj(V3& hb, M33& G, V3 xw, V3 xv, V3 yn_b, V3
 // Io = R Ic R^T + m(|c|^2 1 - c c^T), c = P + R com to the pose); and the
 // reverse of link i's contacts (their external wrench enters F_i with a
 // minus).  Stores link i's V_bar, R_bar and P_bar accumulators.
+// The joint forces of DOF d (actuation, limit penalty, damping): their
+// cotangents from tau_bar = lambda_d.
+template <class Mem>
+__device__ __forceinline__ void dof_adj_force(const DevModel& M, const Mem& w, int d) {
+  const float lam = w[M.o_LAM + d];
+  const int a = __ldg(M.dof_act + d);
+  if (a >= 0) w[M.o_ACTB + a] += lam * __ldg(M.gear + d);
+  const int i = __ldg(M.dof_link + d), jt = __ldg(M.jtype + i);
+  if (jt == J_REV || jt == J_PRIS) {
+    const int s = __ldg(M.qs + i);
+    const float q = w[M.o_Q + s];
+    if (q < __ldg(M.qlo + d) || q > __ldg(M.qhi + d)) w[M.o_QB + s] -= lam * M.klim;
+  }
+  w[M.o_QDB + d] -= lam * __ldg(M.damp + d);
+}
+
 template <class Mem>
 __device__ __forceinline__ void lk_adj_local(const DevModel& M, const Mem& w, int i) {
-  const int d0 = __ldg(M.ds + i), nd = __ldg(M.nd + i), jt = __ldg(M.jtype + i);
-  for (int d = d0; d < d0 + nd; ++d) {
-    const float lam = w[M.o_LAM + d];
-    const int a = __ldg(M.dof_act + d);
-    if (a >= 0) w[M.o_ACTB + a] += lam * __ldg(M.gear + d);
-    if (jt == J_REV || jt == J_PRIS) {
-      const int s = __ldg(M.qs + i);
-      const float q = w[M.o_Q + s];
-      if (q < __ldg(M.qlo + d) || q > __ldg(M.qhi + d)) w[M.o_QB + s] -= lam * M.klim;
-    }
-    w[M.o_QDB + d] -= lam * __ldg(M.damp + d);
-  }
+  const int jt = __ldg(M.jtype + i);
   const int osi = M.o_SI + 10 * i;
   const float m = w[osi];
   const V3 h = ld3(w, osi + 1);
@@ -1418,7 +1423,10 @@ __device__ __forceinline__ void st_dynamics_adj(const DevModel& M, const Mem& w,
     }
     team_sync(nl);
   }
+  // one pass: links from the first lane up, DOFs' joint forces from the last
+  // lane down (a free root's six DOFs do not load the root's lane)
   for (int i = lane; i < M.L; i += nl) lk_adj_local(M, w, i);
+  for (int d = nl - 1 - lane; d < M.nv; d += nl) dof_adj_force(M, w, d);
   team_sync(nl);
   if (M.nseg > 0) {
     for (int sg = lane; sg < M.nseg; sg += nl) seg_adjoint(M, w, sg);

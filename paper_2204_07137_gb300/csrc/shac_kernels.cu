@@ -14,10 +14,10 @@ namespace shac {
 
 // Register caps of the batched kernels (forward, adjoint): the live state of
 // the chain carries and of the 32-row dense path fits without spills; the
-// host launches at most 8 warps per CTA (8 x 32 x 200 registers fit an SM's
+// host launches at most 8 warps per CTA (8 x 32 x 208 registers fit an SM's
 // 64 Ki).
 #define BATCHED_REGS_FORWARD 184
-#define BATCHED_REGS_ADJOINT 200
+#define BATCHED_REGS_ADJOINT 208
 
 // ------------------------------------------------------------------ PLAIN --
 

@@ -2,9 +2,9 @@
 Algorithm 1, appendix A.1 and the hyperparameter tables of the appendix).
 
 One learning episode:
-  1. roll out N trajectories of h steps with the stochastic policy from the end
-     states of the previous episode (Sec. 3.2: gradients are cut between
-     learning episodes), each step through ``SimStep`` (the library's step, its
+  1. roll out N trajectories of h steps with the stochastic policy, each
+     continuing where the last episode's trajectory stopped (Sec. 3.2:
+     gradients are cut between learning episodes), each step through ``SimStep`` (the library's step, its
      backward the library's step adjoint); an environment whose task ends
      (root below the task height, or the task horizon) restarts from a fresh
      seeded initial state, which cuts the gradient there;

@@ -60,8 +60,8 @@ ALGO_FLOPS_PER_ENV_STEP = {
 # DRAM traffic (read + write) of one launch of each batched kernel on the full
 # 32-step ant-2048 window with the window tape (one-pass ncu capture of that
 # launch); profiles/batched_ant_2048.md.
-TRAFFIC_BYTES_PER_LAUNCH = {"ant-2048": {"k_batched_forward": 8.36e6 + 2.81e9,
-                                         "k_batched_adjoint": 2.89e9 + 3.16e6}}
+TRAFFIC_BYTES_PER_LAUNCH = {"ant-2048": {"k_batched_forward": 9.46e6 + 2.81e9,
+                                         "k_batched_adjoint": 2.89e9 + 2.72e6}}
 
 # Algorithmic HBM bytes per env-step (ant): forward reads the action (8 f32)
 # and writes the checkpoint (29) and reward (1); the adjoint reads checkpoint

@@ -533,6 +533,18 @@ def gpu_main(args, rank, world, dist):
     hbm_bytes = traffic if traffic is not None else \
         (ALGO_BYTES_PER_ENV_STEP.get(dominant, 0) + tape_bytes) * n_envs * H
     hbm_gbs = hbm_bytes / (ms_dom * 1e-3) / 1e9
+    # the window's algorithmic work (forward + reverse) over each form's window
+    # time: the same numerator for both forms, whatever each recomputes
+    wf = None if counts is None else counts["forward"] + counts["adjoint"]
+
+    def window_roofline(ms):
+        if wf is None:
+            return None
+        a = wf * env_steps / (ms * 1e-3) / 1e12
+        return {"bound": "alu", "achieved": a, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": a / FP32_PEAK_TFLOPS, "algo_flops_per_env_step": wf,
+                "peak_source": "derived FP32 peak: 152 SMs x 128 lanes x 2 x 2.07 GHz"}
+
     line = {
         "metric": METRIC, "value": value, "unit": "env-steps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_batched, "higher_is_better": True, "scaling": "weak",
@@ -545,7 +557,8 @@ def gpu_main(args, rank, world, dist):
                    "warps_per_cta": sim.get_launch(0)[1], "l2": "flushed (256 MB write) before each timed step",
                    "parallelism": f"env-sharded replicas x{world}"},
         "plain_form": {"value": plain_value, "unit": "env-steps/s", "ms_per_step": ms_plain,
-                       "steps": args.plain_steps},
+                       "steps": args.plain_steps, "window_roofline": window_roofline(ms_plain)},
+        "window_roofline": window_roofline(ms_batched),
         "speedup_vs_plain": value / plain_value,
         "recompute_window": {"value": env_steps / (ms_recompute * 1e-3), "unit": "env-steps/s",
                              "ms_per_step": ms_recompute, "bitwise_equal_to_taped": bool(same),

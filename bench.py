@@ -87,7 +87,7 @@ def parse():
     p.add_argument("--steps", type=int, default=40)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    p.add_argument("--plain-steps", type=int, default=2)
+    p.add_argument("--plain-steps", type=int, default=20)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--workload", default=WORKLOAD)
     p.add_argument("--grad-check-envs", type=int, default=4,
@@ -160,6 +160,20 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------- reference --
+def host_cpu_model() -> str:
+    """The host CPU's model name as lscpu reports it (Arm cores report no name
+    in /proc/cpuinfo), else the machine type."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.strip().startswith("Model name:"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+    return platform.machine()
+
+
 def oracle_window_rate(model, n_envs: int, seed: int = 0, target_s: float = 12.0):
     """env-steps/s of the FP64 oracle (window forward + exact adjoint) on a
     bounded sample of the workload: hs steps of n environments, starting from
@@ -233,7 +247,7 @@ def reference_main(args, rank, world):
                    "substeps": model.substeps if len(wl.groups) == 1 else [m.substeps for m, _ in wl.groups],
                    "form": "FP64 CPU oracle, forward + dual-number exact adjoint"},
         "cpu_baseline": {"value": value, "unit": "env-steps/s", "cores": threads, "kind": "oracle",
-                         "sample": f"{samples[0]} per timed step"},
+                         "cpu_model": host_cpu_model(), "sample": f"{samples[0]} per timed step"},
         "e2e": {"value": value, "unit": "env-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -489,7 +503,7 @@ def gpu_main(args, rank, world, dist):
         plain.window_forward(q0, qd0, act, out=pf, stream=stream)
         plain.window_adjoint(pf[0], pf[1], act, rbar, zq, zqd, out=pa, stream=stream)
 
-    ms_plain = timed(plain_step, args.plain_steps, 1)
+    ms_plain = timed(plain_step, args.plain_steps, args.warmup)
 
     # ---- end to end through the public API with pinned host buffers
     hq0 = q0.cpu().pin_memory()
@@ -585,6 +599,7 @@ def gpu_main(args, rank, world, dist):
     if not args.no_cpu_baseline:
         r, threads, dt, desc = oracle_workload_rate(groups, seed=0, target_s=12.0)
         line["cpu_baseline"] = {"value": r, "unit": "env-steps/s", "cores": threads, "kind": "oracle",
+                                "cpu_model": host_cpu_model(),
                                 "sample": f"{desc}, forward + exact adjoint, {dt:.1f} s",
                                 "single_core": oracle_single_core_rate(args.workload)}
     print(json.dumps(line), flush=True)

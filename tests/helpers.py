@@ -77,3 +77,20 @@ def seeded_case(model, n, seed, kind="initial"):
             q[2] = model.root_z + np.float32(0.3)   # above the ground
     act = I.window_actions(model, n, 1, seed)[0]
     return q, qd, act
+
+
+def long_chain(n_hinges):
+    """A free root (sphere, r 0.1 m) carrying one chain of n_hinges hinges
+    (alternating y / x axes, 0.05 m capsules): nv = 6 + n_hinges.  Armature
+    0.1 keeps cond(M + diag(arm)) near 200, under the ant-like model's, so
+    FP32 parity holds at the usual tolerances."""
+    b = I._Builder("chain")
+    m, c, J = I.sphere_mass_inertia(0.1, 1000.0)
+    parent = b.link(-1, I.FREE, mass=m, com=c, inertia=J)
+    for k in range(n_hinges):
+        mk, ck, Jk = I.capsule_mass_inertia(0.02, (0, 0, 0), (0, 0, -0.05), 1000.0)
+        parent = b.link(parent, I.REVOLUTE, axis=(0, 1, 0) if k % 2 == 0 else (1, 0, 0),
+                        pos=(0, 0, -0.1 if k == 0 else -0.05), mass=mk, com=ck, inertia=Jk)
+    nv = 6 + n_hinges
+    return b.finish(act_dof=list(range(6, nv)), act_gear=[5.0] * n_hinges, dt=I.CONTROL_DT, substeps=4,
+                    armature=0.1, damping=0.1, root_z=5.0)

@@ -63,6 +63,11 @@ def test_model_validation_on_host(lib):
             _lib.ModelHandle(I.hopper().replace(**kw))
         assert e.value.status == 2
     assert _lib.status_string(5) == "capacity exceeded"
+    from helpers import long_chain
+    assert _lib.ModelHandle(long_chain(26)).nv == 32        # the compiled maximum
+    with pytest.raises(_lib.ShacError) as e:
+        _lib.ModelHandle(long_chain(27))                     # 33 DOF
+    assert e.value.status == 5
 
 
 def test_product_path_does_not_use_the_oracle():

@@ -1,10 +1,11 @@
-"""Degenerate sizes through the C ABI: a single environment (a team or a
-plain warp with one live lane) against the FP64 oracle, and an empty
-articulation group inside a batch, which must change nothing for the others."""
+"""Degenerate and extreme sizes through the C ABI: a single environment (a
+team or a plain warp with one live lane) and the largest model the library
+accepts (32 DOF) against the FP64 oracle, and an empty articulation group
+inside a batch, which must change nothing for the others."""
 import numpy as np
 import pytest
 
-from helpers import assert_grad_close, assert_state_close, model_by_name, seeded_case
+from helpers import assert_grad_close, assert_state_close, long_chain, model_by_name, seeded_case
 from paper_2204_07137_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
@@ -78,3 +79,32 @@ def test_empty_group_changes_nothing(form):
         outs.append([x.cpu().numpy() for x in list(f) + list(g)])
     for a, b in zip(*outs):
         np.testing.assert_array_equal(a, b)
+
+
+@pytest.mark.parametrize("form", ["plain", "batched"])
+def test_largest_model_step_and_adjoint(oracle_mod, form):
+    """32 DOF, the compiled maximum: the batched form runs its widest
+    register dense path (32 rows, one environment per warp)."""
+    m = long_chain(26)
+    assert m.nv == 32
+    N = 3
+    sim = make_sim([(m, N)], form)
+    o = oracle_mod.Oracle(m)
+    q, qd = I.initial_state(m, N, 2)
+    a = I.window_actions(m, N, 1, 2)[0]
+    qn, qdn, r = sim.step(T(q), T(qd), T(a))
+    torch.cuda.synchronize()
+    rq, rqd, rr = o.step(q.T, qd.T, a.T)
+    assert_state_close(qn.cpu().numpy().reshape(m.nq, N).T, rq, f"chain32/{form} q_next")
+    assert_state_close(qdn.cpu().numpy().reshape(m.nv, N).T, rqd, f"chain32/{form} qd_next")
+    rng = np.random.default_rng(3)
+    qb = rng.normal(size=(m.nq, N)).astype(np.float32)
+    qdb = rng.normal(size=(m.nv, N)).astype(np.float32)
+    rb = rng.normal(size=N).astype(np.float32)
+    gq, gqd, ga = sim.step_adjoint(T(q), T(qd), T(a), T(qb), T(qdb), T(rb))
+    torch.cuda.synchronize()
+    sq, sqd, sa = o.step_vjp(q.T, qd.T, a.T, qb.T, qdb.T, rb)
+    got = np.concatenate([gq.cpu().numpy().reshape(m.nq, N), gqd.cpu().numpy().reshape(m.nv, N),
+                          ga.cpu().numpy().reshape(m.na, N)])
+    assert_grad_close(got, np.concatenate([sq.T, sqd.T, sa.T]), f"chain32/{form} step adjoint")
+    assert sim.status() == 0

@@ -123,17 +123,26 @@ class GaussianPolicy(nn.Module):
         return torch.tanh(self.mu(obs) + torch.exp(self.log_std) * eps)
 
 
-def observation(model, q: torch.Tensor, qd: torch.Tensor) -> torch.Tensor:
+def observation(model, q: torch.Tensor, qd: torch.Tensor, a_prev: torch.Tensor | None = None) -> torch.Tensor:
     """Observation of a single-group state block (q [nq, N], qd [nv, N]) ->
-    [N, n_obs]: free-root models as in the appendix A.3 tables
-    (``policy.free_root_observation``); the cart-pole as in its A.3 table (x,
-    x_dot, sin theta, cos theta, theta_dot); others their coordinates and
-    velocities."""
+    [N, n_obs], as the appendix A.3 observation tables list it: free-root
+    models the root height, quaternion, world linear and angular velocity,
+    joint angles and velocities, up and heading projections
+    (``policy.free_root_observation``), and for torque-actuated ones the
+    previous step's actions a_prev [N, na]; planar models everything but the
+    forward position (height, pitch, joints and all velocities); the cart-pole
+    x, x_dot, sin theta, cos theta, theta_dot."""
+    N = q.shape[1]
     if int(model.joint_type[0]) == I.FREE:
-        return free_root_observation(q, qd)
+        o = free_root_observation(q, qd)
+        if len(model.muscle_fmax) == 0:   # torque actuation: the last actions are observed
+            if a_prev is None:
+                a_prev = torch.zeros(N, model.na, device=q.device, dtype=q.dtype)
+            o = torch.cat([o, a_prev], dim=1)
+        return o
     if model.name == "cartpole":
         return torch.stack([q[0], qd[0], torch.sin(q[1]), torch.cos(q[1]), qd[1]], dim=0).transpose(0, 1)
-    return torch.cat([q, qd], dim=0).transpose(0, 1)
+    return torch.cat([q[1:], qd], dim=0).transpose(0, 1)
 
 
 class SHAC:
@@ -161,7 +170,8 @@ class SHAC:
         q, qd = self._initial(0)
         self.q, self.qd = q, qd
         self.e = torch.from_numpy(np.random.default_rng(seed).integers(0, self.horizon, self.N)).to(dev)
-        n_obs = observation(model, q.view(model.nq, self.N), qd.view(model.nv, self.N)).shape[1]
+        self.a_prev = torch.zeros(self.N, model.na, device=dev)   # last actions (observed by torque models)
+        n_obs = self._obs(q, qd, self.a_prev).shape[1]
         self.actor = GaussianPolicy(n_obs, model.na).to(dev)
         self.critic = mlp([n_obs, 64, 64, 1]).to(dev)
         self.target = mlp([n_obs, 64, 64, 1]).to(dev)
@@ -179,8 +189,8 @@ class SHAC:
         q, qd = I.initial_state(self.model, self.N, self.seed * 1000 + k)
         return (torch.from_numpy(q.reshape(-1)).to(self.device), torch.from_numpy(qd.reshape(-1)).to(self.device))
 
-    def _obs(self, q, qd):
-        return observation(self.model, q.view(self.model.nq, self.N), qd.view(self.model.nv, self.N))
+    def _obs(self, q, qd, a_prev):
+        return observation(self.model, q.view(self.model.nq, self.N), qd.view(self.model.nv, self.N), a_prev)
 
     @torch.no_grad()
     def evaluate(self, steps: int, seed: int) -> float:
@@ -189,9 +199,10 @@ class SHAC:
         m, N = self.model, self.N
         q, qd = (torch.from_numpy(x.reshape(-1)).to(self.device) for x in I.initial_state(m, N, 10_000 + seed))
         zero = torch.zeros(N, m.na, device=self.device)
+        a = zero
         tot = 0.0
         for _ in range(steps):
-            a = self.actor(self.norm(self._obs(q, qd)), zero)
+            a = self.actor(self.norm(self._obs(q, qd, a)), zero)
             q, qd, r = self.sim.step(q, qd, a.transpose(0, 1).contiguous().view(-1))
             tot += float(r.mean())
         return tot / steps
@@ -208,12 +219,13 @@ class SHAC:
         ev[0].record()
         # 1-2. rollout through the differentiable simulator and the policy loss
         q, qd = self.q, self.qd                                  # detached: cut between episodes
+        a_prev = self.a_prev
         q_reset, qd_reset = self._initial(1 + self.episode_index)
         disc = torch.ones(N, device=self.device)
         total = torch.zeros(N, device=self.device)
         obs_raw, rews, dones = [], [], []
         for t in range(h):
-            o = self._obs(q, qd)
+            o = self._obs(q, qd, a_prev)
             obs_raw.append(o.detach())
             eps = torch.randn(N, m.na, device=self.device, generator=self.rng)
             a = self.actor(self.norm(o), eps)
@@ -230,9 +242,10 @@ class SHAC:
             dqd = d.repeat(m.nv)
             q = torch.where(dq, q_reset, qn)
             qd = torch.where(dqd, qd_reset, qdn)
+            a_prev = torch.where(d[:, None], torch.zeros_like(a), a)   # a new episode starts with no action
             rews.append(r.detach())
             dones.append(d)
-        o_end = self._obs(q, qd)
+        o_end = self._obs(q, qd, a_prev)
         obs_raw.append(o_end.detach())
         v_end = self.target(self.norm(o_end)).squeeze(-1)
         total = total + disc * v_end
@@ -244,7 +257,7 @@ class SHAC:
         if self.grad_clip is not None:
             nn.utils.clip_grad_norm_(self.actor.parameters(), self.grad_clip)
         self.actor_opt.step()
-        self.q, self.qd = q.detach(), qd.detach()
+        self.q, self.qd, self.a_prev = q.detach(), qd.detach(), a_prev.detach()
         ev[2].record()
         # 4-6. critic: TD-lambda targets with the target critic, fit, soft update
         with torch.no_grad():

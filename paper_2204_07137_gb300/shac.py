@@ -96,7 +96,20 @@ class RunningNorm:
         self.count = tot
 
 
+# Policy and value network hidden sizes per task (appendix table of network
+# settings); tasks it does not list take the ant's setting.
+PAPER_NETWORKS = {
+    "cartpole": ((64, 64), (64, 64)),
+    "ant": ((128, 64, 32), (64, 64)),
+    "humanoid": ((256, 128), (128, 128)),
+    "mtu": ((512, 256), (256, 256)),
+}
+GENERAL_NETWORKS = PAPER_NETWORKS["ant"]
+
+
 def mlp(sizes, out_scale: float = 1.0):
+    """Linear layers with an ELU and a layer normalisation after every hidden
+    layer (appendix: ELU hidden activations, each hidden layer normalised)."""
     layers = []
     for k, (a, b) in enumerate(zip(sizes[:-1], sizes[1:])):
         lin = nn.Linear(a, b)
@@ -107,6 +120,7 @@ def mlp(sizes, out_scale: float = 1.0):
         layers.append(lin)
         if k < len(sizes) - 2:
             layers.append(nn.ELU())
+            layers.append(nn.LayerNorm(b))
     return nn.Sequential(*layers)
 
 
@@ -172,9 +186,10 @@ class SHAC:
         self.e = torch.from_numpy(np.random.default_rng(seed).integers(0, self.horizon, self.N)).to(dev)
         self.a_prev = torch.zeros(self.N, model.na, device=dev)   # last actions (observed by torque models)
         n_obs = self._obs(q, qd, self.a_prev).shape[1]
-        self.actor = GaussianPolicy(n_obs, model.na).to(dev)
-        self.critic = mlp([n_obs, 64, 64, 1]).to(dev)
-        self.target = mlp([n_obs, 64, 64, 1]).to(dev)
+        pol_hidden, val_hidden = PAPER_NETWORKS.get(model.name, GENERAL_NETWORKS)
+        self.actor = GaussianPolicy(n_obs, model.na, hidden=pol_hidden).to(dev)
+        self.critic = mlp([n_obs, *val_hidden, 1]).to(dev)
+        self.target = mlp([n_obs, *val_hidden, 1]).to(dev)
         self.target.load_state_dict(self.critic.state_dict())
         for p in self.target.parameters():
             p.requires_grad_(False)

@@ -18,7 +18,7 @@ def _table():
         if not ln or ln.startswith("#"):
             continue
         table, task, key, val = ln.split()
-        rows[(table, task, key)] = float(val)
+        rows[(table, task, key)] = tuple(int(x) for x in val.split(",")) if table == "network" else float(val)
     return rows
 
 
@@ -26,7 +26,7 @@ def test_per_task_and_general_settings_match_the_paper():
     from paper_2204_07137_gb300 import shac
     rows = _table()
     for (table, task, key), val in rows.items():
-        if key not in ("actor_lr", "critic_lr", "alpha", "episodes"):
+        if table == "network" or key not in ("actor_lr", "critic_lr", "alpha", "episodes"):
             continue
         hp = shac.GENERAL_HPARAMS if table == "general" else shac.PAPER_HPARAMS[task]
         assert hp[key] == pytest.approx(val, rel=0, abs=0), (table, task, key)
@@ -47,3 +47,21 @@ def test_learner_defaults_match_the_paper():
     assert d["critic_minibatches"] == rows[("general", "any", "critic_minibatches")]
     assert tuple(d["betas"]) == (rows[("optimal", "cartpole", "adam_beta1")],
                                  rows[("optimal", "cartpole", "adam_beta2")])
+
+
+def test_network_sizes_match_the_paper():
+    from paper_2204_07137_gb300 import shac
+    for (table, task, key), val in _table().items():
+        if table != "network":
+            continue
+        pol, vf = shac.PAPER_NETWORKS[task]
+        assert (pol if key == "policy" else vf) == val, (task, key)
+
+
+def test_hidden_layers_are_elu_then_layer_norm():
+    import torch
+    from paper_2204_07137_gb300 import shac
+    net = shac.mlp([5, 64, 32, 1])
+    kinds = [type(m) for m in net]
+    assert kinds == [torch.nn.Linear, torch.nn.ELU, torch.nn.LayerNorm, torch.nn.Linear, torch.nn.ELU,
+                     torch.nn.LayerNorm, torch.nn.Linear]

@@ -1054,16 +1054,9 @@ __device__ __forceinline__ void si_adj(V3& hb, M33& G, V3 xw, V3 xv, V3 yn_b, V3
   add_outer(G, yn_b, xw);
 }
 
-// lk_adj_local, one lane per link, everything of adjoint sweep 1 that is local
-// to link i: the joint forces of its DOFs (actuation, limits, damping:
-// tau_j_bar = lambda); the local force F_i = I A + V x* (I V) - Fext
-// recomputed with the solved accelerations; the reverse of F_i (A_bar =
-// I F_bar, V_bar and the inertia cotangent, carried through h = m c,
-// Io = R Ic R^T + m(|c|^2 1 - c c^T), c = P + R com to the pose); and the
-// reverse of link i's contacts (their external wrench enters F_i with a
-// minus).  Stores link i's V_bar, R_bar and P_bar accumulators.
 // The joint forces of DOF d (actuation, limit penalty, damping): their
-// cotangents from tau_bar = lambda_d.
+// cotangents from tau_bar = lambda_d.  One lane per DOF, in the same pass as
+// lk_adj_local (the two write disjoint scratch).
 template <class Mem>
 __device__ __forceinline__ void dof_adj_force(const DevModel& M, const Mem& w, int d) {
   const float lam = w[M.o_LAM + d];
@@ -1078,6 +1071,13 @@ __device__ __forceinline__ void dof_adj_force(const DevModel& M, const Mem& w, i
   w[M.o_QDB + d] -= lam * __ldg(M.damp + d);
 }
 
+// lk_adj_local, one lane per link, everything of adjoint sweep 1 that is local
+// to link i but its DOFs' joint forces (dof_adj_force): the local force
+// F_i = I A + V x* (I V) - Fext recomputed with the solved accelerations; the
+// reverse of F_i (A_bar = I F_bar, V_bar and the inertia cotangent, carried
+// through h = m c, Io = R Ic R^T + m(|c|^2 1 - c c^T), c = P + R com to the
+// pose); and the reverse of link i's contacts (their external wrench enters
+// F_i with a minus).  Stores link i's V_bar, R_bar and P_bar accumulators.
 template <class Mem>
 __device__ __forceinline__ void lk_adj_local(const DevModel& M, const Mem& w, int i) {
   const int jt = __ldg(M.jtype + i);

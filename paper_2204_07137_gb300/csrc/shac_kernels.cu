@@ -208,8 +208,8 @@ __device__ __forceinline__ void record_save(float* dst, const SMem& w, int n, in
 }
 
 // One work item of the forward window (all steps, all substeps).
-__device__ __forceinline__ void forward_item(const BatchedArgs& a, const DevModel& M, const WorkItem& it, const SMem& w,
-                             const Team& t) {
+__device__ __forceinline__ void forward_item(const BatchedArgs& a, const DevModel& M, const WorkItem& it,
+                                             const SMem& w, const Team& t) {
   const int nm = a.dense_nm[it.group];
   const GroupIO& io = a.io.g[it.group];
   team_load(w, M.o_Q, a.q_in + io.q_off, M.nq, io.N, t.env, t.lane, t.nl);
@@ -288,8 +288,8 @@ __device__ __forceinline__ void record_load(const SMem& w, const float* src, int
 // the workspace and reloaded by the reverse pass.  With the window tape the
 // forward window already kept every record (and the post-step state), and the
 // recompute is skipped.
-__device__ __forceinline__ void adjoint_item(const BatchedArgs& a, const DevModel& M, const WorkItem& it, const SMem& w,
-                             const Team& t) {
+__device__ __forceinline__ void adjoint_item(const BatchedArgs& a, const DevModel& M, const WorkItem& it,
+                                             const SMem& w, const Team& t) {
   const int nm = a.dense_nm[it.group];
   const GroupIO& io = a.io.g[it.group];
   const int REC = M.rec_floats;

@@ -266,6 +266,26 @@ shac_status shac_batch_set_launch(shac_batch* batch, int32_t group, int32_t lane
 shac_status shac_batch_get_launch(const shac_batch* batch, int32_t group, int32_t* lanes_per_env,
                                   int32_t* warps_per_cta);
 
+/* Measured choice of the batched launch shape (the environment-to-warp
+ * packing per group and the CTA size; the paper has no counterpart: its
+ * kernels are one thread per environment).  Coordinate descent: each group's
+ * lanes per environment in turn (1, 2, 4, 8, 16, 32; the others fixed), then
+ * the warps per CTA (1, 2, 4, 8); every candidate is timed as a window forward
+ * + window adjoint of min(h_max, 4) steps with CUDA events on `stream` (one
+ * warm-up, best of two), from the rest configuration (joint coordinates 0,
+ * free joints at the origin with the identity orientation, zero velocities and
+ * actions).  The fastest shape is applied to the batch (as
+ * shac_batch_set_launch would) and kept.  `workspace`: the caller's workspace
+ * of shac_batch_workspace_bytes (256-byte aligned), overwritten.  budget_ms:
+ * wall-clock limit of the search (> 0; the best shape found so far is kept
+ * when it runs out).  Synchronises the stream and allocates and frees
+ * temporary device buffers for the inputs and outputs of the timed windows, so
+ * it must not be called during a stream capture.  A PLAIN batch, or one with
+ * no environment, returns SHAC_OK unchanged.  Errors: SHAC_ERR_INVALID_ARG for
+ * a null batch, an unaligned workspace or budget_ms <= 0; SHAC_ERR_CUDA if a
+ * CUDA call fails (the launch shape is then left as it was). */
+shac_status shac_autotune(shac_batch* batch, void* stream, void* workspace, int32_t budget_ms);
+
 /* Window tape (BATCHED form; SHAC_ERR_UNSUPPORTED for PLAIN): keep = 1 makes
  * shac_window_forward (and its episodic variant) store every substep record of
  * every step (link poses, inertias, subspaces, velocities, external wrenches,

@@ -1,5 +1,6 @@
 // Host side of the C ABI declared in include/shacsim.h.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -821,4 +822,108 @@ extern "C" const char* shac_status_string(shac_status s) {
     case SHAC_ERR_UNSUPPORTED: return "unsupported";
   }
   return "unknown status";
+}
+
+// -------------------------------------------------------------- autotune --
+extern "C" shac_status shac_autotune(shac_batch* b, void* stream, void* ws, int32_t budget_ms) {
+  if (!b || !aligned_ws(b, ws) || budget_ms <= 0) return SHAC_ERR_INVALID_ARG;
+  if (b->form != SHAC_FORM_BATCHED || b->n_items == 0) return SHAC_OK;
+  const auto t0 = std::chrono::steady_clock::now();
+  auto out_of_time = [&]() {
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count() > budget_ms;
+  };
+  cudaStream_t s = (cudaStream_t)stream;
+  const int h = std::min(b->h_max, 4);
+  // inputs and outputs of the timed windows, in one temporary allocation
+  const size_t nq = (size_t)b->q_size, nqd = (size_t)b->qd_size, na = (size_t)b->act_size, ne = (size_t)b->n_envs;
+  const size_t parts[] = {nq, nqd, h * na, (h + 1) * nq, (h + 1) * nqd, h * ne, h * ne, (h + 1) * nq,
+                          (h + 1) * nqd, nq, nqd, h * na};
+  size_t total = 0;
+  for (size_t p : parts) total += (p + 63) / 64 * 64;
+  float* buf = nullptr;
+  if (cudaMalloc(&buf, total * sizeof(float)) != cudaSuccess) return SHAC_ERR_CUDA;
+  float* ptr[12];
+  {
+    size_t off = 0;
+    for (int k = 0; k < 12; ++k) { ptr[k] = buf + off; off += (parts[k] + 63) / 64 * 64; }
+  }
+  float *q0 = ptr[0], *qd0 = ptr[1], *act = ptr[2], *qt = ptr[3], *qdt = ptr[4], *rew = ptr[5], *rbar = ptr[6];
+  float *qtb = ptr[7], *qdtb = ptr[8], *q0b = ptr[9], *qd0b = ptr[10], *actb = ptr[11];
+  // rest configuration: free joints at the origin with the identity quaternion (x, y, z, w: w = 1)
+  std::vector<float> qh(nq, 0.f);
+  for (int gi = 0; gi < (int)b->groups.size(); ++gi) {
+    const Group& g = b->groups[gi];
+    for (int i = 0; i < g.m->L; ++i)
+      if (g.m->jtype[i] == J_FREE)
+        for (int e = 0; e < g.N; ++e) qh[(size_t)b->io.g[gi].q_off + (size_t)(g.m->qs[i] + 6) * g.N + e] = 1.f;
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  shac_status st = cuda_ok(cudaMemsetAsync(buf, 0, total * sizeof(float), s));
+  if (st == SHAC_OK) st = cuda_ok(cudaMemcpyAsync(q0, qh.data(), nq * sizeof(float), cudaMemcpyHostToDevice, s));
+  if (st == SHAC_OK) st = cuda_ok(cudaEventCreate(&e0));
+  if (st == SHAC_OK) st = cuda_ok(cudaEventCreate(&e1));
+  auto window = [&]() -> shac_status {
+    shac_status r = run_forward(b, s, ws, h, q0, qd0, act, qt + nq, qdt + nqd, rew, qt, qdt, nullptr, true);
+    if (r != SHAC_OK) return r;
+    return run_adjoint(b, s, ws, h, qt, qdt, act, rbar, qtb, qdtb, qtb + (size_t)h * nq, qdtb + (size_t)h * nqd,
+                       q0b, qd0b, actb, nullptr, true);
+  };
+  // ms per window of the current shape (infinite if the shape does not launch)
+  auto measure = [&](float* ms) -> shac_status {
+    *ms = INFINITY;
+    shac_status r = window();
+    if (r == SHAC_ERR_CAPACITY) return SHAC_OK;
+    if (r != SHAC_OK) return r;
+    for (int rep = 0; rep < 2; ++rep) {
+      if (cudaEventRecord(e0, s) != cudaSuccess) return SHAC_ERR_CUDA;
+      if ((r = window()) != SHAC_OK) return r;
+      if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) return SHAC_ERR_CUDA;
+      float t = 0.f;
+      if (cudaEventElapsedTime(&t, e0, e1) != cudaSuccess) return SHAC_ERR_CUDA;
+      *ms = std::min(*ms, t);
+    }
+    return SHAC_OK;
+  };
+  const int n_groups = (int)b->groups.size();
+  std::vector<int> lanes0(n_groups), best_lanes(n_groups);
+  for (int gi = 0; gi < n_groups; ++gi) lanes0[gi] = best_lanes[gi] = b->groups[gi].lanes;
+  const int warps0 = b->warps_per_cta;
+  int best_warps = warps0;
+  float best = INFINITY;
+  if (st == SHAC_OK) st = measure(&best);
+  static const int kLanes[] = {1, 2, 4, 8, 16, 32};
+  static const int kWarps[] = {1, 2, 4, 8};
+  for (int gi = 0; gi < n_groups && st == SHAC_OK && !out_of_time(); ++gi) {
+    if (b->groups[gi].N == 0) continue;
+    for (int l : kLanes) {
+      if (st != SHAC_OK || out_of_time()) break;
+      if (l == best_lanes[gi]) continue;
+      for (int gj = 0; gj < n_groups; ++gj) b->groups[gj].lanes = best_lanes[gj];
+      b->groups[gi].lanes = l;
+      b->warps_per_cta = best_warps;
+      if ((st = build_items(b)) != SHAC_OK) break;
+      float t;
+      if ((st = measure(&t)) == SHAC_OK && t < best) { best = t; best_lanes[gi] = l; }
+    }
+  }
+  for (int w : kWarps) {
+    if (st != SHAC_OK || out_of_time()) break;
+    if (w == best_warps) continue;
+    for (int gj = 0; gj < n_groups; ++gj) b->groups[gj].lanes = best_lanes[gj];
+    b->warps_per_cta = w;
+    if ((st = build_items(b)) != SHAC_OK) break;
+    float t;
+    if ((st = measure(&t)) == SHAC_OK && t < best) { best = t; best_warps = w; }
+  }
+  // keep the best shape (the starting one after an error)
+  const bool ok = st == SHAC_OK;
+  for (int gj = 0; gj < n_groups; ++gj) b->groups[gj].lanes = ok ? best_lanes[gj] : lanes0[gj];
+  b->warps_per_cta = ok ? best_warps : warps0;
+  const shac_status st_items = build_items(b);
+  cudaStreamSynchronize(s);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(buf);
+  if (st != SHAC_OK) return st;
+  return st_items;
 }

@@ -74,6 +74,16 @@ class Simulator:
         _lib.check(_lib.load().shac_batch_set_window_tape(self.batch, int(bool(keep))), "shac_batch_set_window_tape")
         self._alloc_workspace()
 
+    def autotune_native(self, budget_ms: int = 2000, stream=None):
+        """The library's own measured launch-shape search (shac_autotune):
+        lanes per environment for each group, then warps per CTA, timed as short
+        windows from the rest configuration; the fastest shape stays applied.
+        Synchronises; not for a stream capture."""
+        _lib.check(_lib.load().shac_autotune(self.batch, self._stream(stream), self._ws(), int(budget_ms)),
+                   "shac_autotune")
+        self._alloc_workspace()
+        return [self.get_launch(g) for g in range(len(self.groups))]
+
     def get_launch(self, group: int) -> Tuple[int, int]:
         l, w = ctypes.c_int32(), ctypes.c_int32()
         _lib.check(_lib.load().shac_batch_get_launch(self.batch, group, ctypes.byref(l), ctypes.byref(w)),

@@ -75,3 +75,36 @@ def test_autotune_picks_a_valid_shape():
     torch.cuda.synchronize()
     for u, v in zip(a, b):
         np.testing.assert_allclose(u.cpu().numpy(), v.cpu().numpy(), rtol=1e-4, atol=1e-3)
+
+
+def test_native_autotune_keeps_a_valid_shape():
+    """shac_autotune (the library's own search) on a heterogeneous batch with
+    the window tape: a valid shape is left applied, the windows it times do not
+    disturb the caller's buffers, and the retuned batch gives the same window up
+    to FP32 reassociation inside a team; a non-positive budget is rejected."""
+    import numpy as np
+    from paper_2204_07137_gb300 import _lib, autotune
+    from paper_2204_07137_gb300.sim import Simulator
+    groups = [(_inputs().cartpole(), 40), (_inputs().ant(), 13)]
+    tuned = Simulator(groups, form="batched", h_max=2)
+    tuned.set_window_tape(True)
+    ref = Simulator(groups, form="batched", h_max=2)
+    ref.set_window_tape(True)
+    x = autotune._Inputs(ref, 2)
+    shapes = tuned.autotune_native(budget_ms=5000)
+    assert len(shapes) == 2
+    assert all(l in autotune.LANES and w in autotune.WARPS for l, w in shapes)
+    a = tuned.window_forward(x.q0, x.qd0, x.act)
+    b = ref.window_forward(x.q0, x.qd0, x.act)
+    torch.cuda.synchronize()
+    for u, v in zip(a, b):
+        np.testing.assert_allclose(u.cpu().numpy(), v.cpu().numpy(), rtol=1e-4, atol=1e-3)
+    assert tuned.status() == 0
+    with pytest.raises(_lib.ShacError) as e:
+        tuned.autotune_native(budget_ms=0)
+    assert e.value.status == 1
+
+
+def _inputs():
+    from paper_2204_07137_gb300 import inputs
+    return inputs

@@ -25,6 +25,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -180,7 +181,8 @@ def oracle_window_rate(model, n_envs: int, seed: int = 0, target_s: float = 12.0
     one environment per oracle thread (the oracle runs environments in
     parallel) and grown (steps first, up to the 32-step window, then
     environments) until the sample takes about target_s / 4 .. target_s of
-    wall time."""
+    wall time; a whole workload that runs faster is repeated until it does.
+    Returns (rate, n, hs, threads, seconds, repeats)."""
     from paper_2204_07137_gb300 import inputs as I
     from oracle import oracle
     o = oracle.Oracle(model)
@@ -204,7 +206,11 @@ def oracle_window_rate(model, n_envs: int, seed: int = 0, target_s: float = 12.0
         else:
             n = min(n_envs, max(n + 1, int(n * grow)))
         dt = run(n, hs)
-    return n * hs / dt, n, hs, threads, dt
+    reps = 1
+    if dt < target_s / 4:   # the whole workload: repeat it
+        reps = max(1, int(math.ceil(target_s / 4 / max(dt, 1e-6))))
+        dt += sum(run(n, hs) for _ in range(reps - 1))
+    return n * hs * reps / dt, n, hs, threads, dt, reps
 
 
 def oracle_workload_rate(groups, seed: int = 0, target_s: float = 12.0):
@@ -215,11 +221,11 @@ def oracle_workload_rate(groups, seed: int = 0, target_s: float = 12.0):
     per = target_s / len(groups)
     total_n, total_t, dts, parts, threads = 0, 0.0, 0.0, [], 1
     for model, n_g in groups:
-        r, n, hs, threads, dt = oracle_window_rate(model, n_g, seed=seed, target_s=per)
+        r, n, hs, threads, dt, reps = oracle_window_rate(model, n_g, seed=seed, target_s=per)
         total_n += n_g
         total_t += n_g / r
         dts += dt
-        parts.append(f"{n} of {n_g} envs ({model.name}) x {hs} steps")
+        parts.append(f"{n} of {n_g} envs ({model.name}) x {hs} steps" + (f" x {reps} runs" if reps > 1 else ""))
     return total_n / total_t, threads, dts, "; ".join(parts)
 
 

@@ -15,7 +15,7 @@ def test_mixed_batch_rate_is_total_envs_over_summed_group_times(monkeypatch):
 
     def fake(model, n_envs, seed=0, target_s=12.0):
         seen.append((model.name, n_envs, target_s))
-        return rates[model.name], 3, 2, 16, 1.0
+        return rates[model.name], 3, 2, 16, 1.0, 1
 
     monkeypatch.setattr(bench, "oracle_window_rate", fake)
     groups = [(SimpleNamespace(name="a"), 4096), (SimpleNamespace(name="b"), 2048), (SimpleNamespace(name="c"), 1024)]
@@ -30,6 +30,6 @@ def test_mixed_batch_rate_is_total_envs_over_summed_group_times(monkeypatch):
 
 def test_single_group_rate_is_the_group_rate(monkeypatch):
     import bench
-    monkeypatch.setattr(bench, "oracle_window_rate", lambda m, n, seed=0, target_s=12.0: (123.0, 8, 4, 16, 2.0))
+    monkeypatch.setattr(bench, "oracle_window_rate", lambda m, n, seed=0, target_s=12.0: (123.0, 8, 4, 16, 2.0, 1))
     r, threads, dt, desc = bench.oracle_workload_rate([(SimpleNamespace(name="ant"), 2048)])
     assert abs(r - 123.0) <= 1e-12 * 123.0 and dt == 2.0 and desc.startswith("8 of 2048 envs (ant) x 4 steps")

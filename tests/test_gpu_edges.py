@@ -108,3 +108,37 @@ def test_largest_model_step_and_adjoint(oracle_mod, form):
                           ga.cpu().numpy().reshape(m.na, N)])
     assert_grad_close(got, np.concatenate([sq.T, sqd.T, sa.T]), f"chain32/{form} step adjoint")
     assert sim.status() == 0
+
+
+@pytest.mark.parametrize("form", ["plain", "batched"])
+def test_two_env_ranges_equal_one_run(form):
+    """Environment sharding by offsets (the multi-GPU split is replicas over
+    env ranges): a window over environments [0, 11) and another over [11, 23),
+    fed the matching slices of the inputs, give bit for bit the full 23-env
+    window's states, rewards and cotangents."""
+    m, N, h, cut = I.ant(), 23, 4, 11
+    q0, qd0 = I.initial_state(m, N, 12)
+    act = I.window_actions(m, N, h, 12)                 # [h, na, N]
+    rng = np.random.default_rng(4)
+    rb = rng.normal(size=(h, N)).astype(np.float32)
+
+    def window(sl):
+        n = sl.stop - sl.start
+        sim = make_sim([(m, n)], form, h)
+        a = T(act[:, :, sl]).view(h, -1)
+        f = sim.window_forward(T(q0[:, sl]), T(qd0[:, sl]), a)
+        zq = torch.zeros(h + 1, sim.q_size, device="cuda")
+        zqd = torch.zeros(h + 1, sim.qd_size, device="cuda")
+        g = sim.window_adjoint(f[0], f[1], a, T(rb[:, sl]).view(h, n), zq, zqd)
+        torch.cuda.synchronize()
+        assert sim.status() == 0
+        qt = f[0].cpu().numpy().reshape(h + 1, m.nq, n)
+        qdt = f[1].cpu().numpy().reshape(h + 1, m.nv, n)
+        ab = g[2].cpu().numpy().reshape(h, m.na, n)
+        return [qt, qdt, f[2].cpu().numpy(), g[0].cpu().numpy().reshape(m.nq, n),
+                g[1].cpu().numpy().reshape(m.nv, n), ab]
+
+    full = window(slice(0, N))
+    parts = [window(slice(0, cut)), window(slice(cut, N))]
+    for k, x in enumerate(full):
+        np.testing.assert_array_equal(x, np.concatenate([parts[0][k], parts[1][k]], axis=-1), err_msg=str(k))

@@ -3,23 +3,29 @@ differentiable simulator on the 2048-environment ant-like workload.
 
 One bench "step" is one pass of the whole hot path over one batch: the
 window forward (32 control steps x 16 substeps, writing the per-step
-checkpoints) followed by the window adjoint (reverse over the 32 steps,
-substeps recomputed from the checkpoints).  value = N * h / time.
+checkpoints) followed by the window adjoint (reverse over the 32 steps, each
+step's substeps recomputed from its checkpoint).  value = N * h / time.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--workload W]
 
-Timed form: BATCHED, both launches captured in one CUDA graph, inputs resident
-in HBM, L2 flushed (256 MB write) before every timed step, CUDA events on the
-launching stream.  The PLAIN form (one env per thread, one kernel per stage
-per substep) is timed on the same inputs for the speed-up.  ``e2e`` repeats
-the measurement through the public API with pinned host buffers: host->device
-copies of (q0, qd0, actions) and device->host copies of (rewards, action and
-initial-state gradients) inside the timed region.
+Timed form (``value``): BATCHED, the configured variant (per-control-step
+checkpoints, substeps recomputed in the adjoint), launch shape chosen by the
+library's autotuner on this batch, both launches captured in one CUDA graph,
+inputs resident in HBM, L2 flushed (256 MB write) before every timed step,
+CUDA events on the launching stream, median over the timed steps.  Also
+reported: the same window with the window tape (every substep record kept in
+HBM, no recompute), the episodic window, the PLAIN form (one env per thread,
+one kernel per stage per substep) on the same inputs for the speed-up, and
+``e2e``: the measurement through the public API with pinned host buffers
+(host->device copies of q0, qd0 and the actions and device->host copies of the
+rewards and of the action and initial-state gradients inside the timed region).
 
 --impl reference times the FP64 CPU oracle (forward + exact adjoint) on the
 host cores on a bounded sample of the same workload.
-Under torchrun each rank simulates its own 2048 environments (weak scaling,
-no collective on the data path); rank 0 prints the line.
+--profile-case runs a few windows of a workload with no timing, for profiler
+captures.
+Under torchrun each rank simulates its own environments (weak scaling, no
+collective on the data path); rank 0 prints the line.
 """
 from __future__ import annotations
 
@@ -43,33 +49,48 @@ WORKLOAD = "ant-2048"
 H = 32
 FLUSH_BYTES = 256 << 20
 
-# FP32 ALU peak of one GB300 from its unit counts and clock: 152 SMs x 128
-# FP32 lanes x 2 flop (FMA) x 2.07 GHz maximum SM clock.
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# FP32 lanes per SM and flops per lane per cycle (one FMA) of the GB300's SMs;
+# the FP32 peak is derived from these, the device's SM count and the maximum
+# SM clock sampled during the run (fp32_peak_tflops).
+FP32_LANES_PER_SM = 128
+FLOPS_PER_LANE_CYCLE = 2
+DEFAULT_SM_MAX_MHZ = 2070.0
 
-# Algorithmic FP32 work per env-step, measured (not estimated): thread-level
-# FADD + FMUL + 2 x FFMA executed by the one-environment-per-thread (PLAIN)
-# stage kernels over one window step, counted by ncu (the command and the
-# per-stage split are in profiles/plain_flops_ant.md).  The timed batched
-# window keeps its substep records (window tape), so the adjoint kernel does
-# the reverse-only stages; the recomputing adjoint would add one forward
-# recompute (134,556).  Workloads without a count report achieved=null.
-ALGO_FLOPS_PER_ENV_STEP = {
-    "ant-2048": {"forward": 134692, "adjoint": 172338},
+# FP32 work per env-step, counted with ncu on the one-environment-per-thread
+# (PLAIN) stage kernels over one window step: thread-level FADD + FMUL +
+# 2 x FFMA, i.e. the work that form executes (it includes whatever redundant
+# work that form does; the FP64 oracle is no op count of this algorithm: it
+# builds M from per-link Jacobians and the bias by vector Newton-Euler, which
+# is other and more work).  "forward": one forward step (K substeps);
+# "reverse": the reverse-only part of one adjoint step; the recomputing
+# adjoint kernel executes one forward recompute + the reverse.
+FLOPS_PER_ENV_STEP = {
+    "ant": {"forward": 134692, "recompute": 134556, "reverse": 172338},
 }
 
-# DRAM traffic (read + write) of one launch of each batched kernel on the full
-# 32-step ant-2048 window with the window tape (one-pass ncu capture of that
-# launch); profiles/batched_ant_2048.md.
-TRAFFIC_BYTES_PER_LAUNCH = {"ant-2048": {"k_batched_forward": 9.46e6 + 2.81e9,
-                                         "k_batched_adjoint": 2.89e9 + 2.72e6}}
+# Algorithmic HBM bytes per env-step (FP32) of one step-level call, the
+# accounting of the hot-path table: the forward reads the state and the action
+# and writes the next state and the reward; the adjoint reads the checkpoint,
+# the action, the next state's cotangent and the reward cotangent and writes the
+# state and action cotangents (ant-like model: 268 + 416 = 684 B).  The window
+# kernels move less (the state stays on chip between steps).  The substep
+# records a kernel keeps in the workspace (one step's worth for the recomputing
+# adjoint, the whole window with the window tape) are scratch traffic, reported
+# beside.
+def algo_bytes_per_env_step(model):
+    s = model.nq + model.nv
+    return {"forward": 4 * (2 * s + model.na + 1), "adjoint": 4 * (3 * s + 2 * model.na + 1)}
 
-# Algorithmic HBM bytes per env-step (ant): forward reads the action (8 f32)
-# and writes the checkpoint (29) and reward (1); the adjoint reads checkpoint
-# (29), action (8) and reward cotangent (1) and writes the action cotangent (8).
-# With the window tape both kernels add the tape bytes of an env-step (written
-# by the forward, read by the adjoint), measured from the workspace size.
-ALGO_BYTES_PER_ENV_STEP = {"k_batched_forward": 4 * (8 + 29 + 1), "k_batched_adjoint": 4 * (29 + 8 + 1 + 8)}
+
+# DRAM traffic (read + write) per launch of the batched kernels on the full
+# ant-2048 h = 32 window, from one-pass ncu captures (dram__bytes_read.sum +
+# dram__bytes_write.sum of one launch); None where no capture of the current
+# kernels exists.
+TRAFFIC_BYTES_PER_LAUNCH = {"ant-2048": {"forward": None, "adjoint_recompute": None, "adjoint_tape": None}}
+
+
+def fp32_peak_tflops(n_sms: int, sm_mhz: float) -> float:
+    return n_sms * FP32_LANES_PER_SM * FLOPS_PER_LANE_CYCLE * sm_mhz * 1e6 / 1e12
 
 
 def measured_hbm_gbs():
@@ -92,7 +113,20 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--workload", default=WORKLOAD)
     p.add_argument("--grad-check-envs", type=int, default=4,
-                   help="sampled environments of the first group checked against the oracle (0: skip)")
+                   help="sampled environments of every group checked against the oracle (0: skip)")
+    p.add_argument("--autotune-ms", type=int, default=5000,
+                   help="wall-clock budget of the library's launch-shape search on the timed batch (0: default shape)")
+    p.add_argument("--profile-case", action="store_true",
+                   help="run --pc-reps windows of the workload through the public API, no timing or checks "
+                        "(for profiler captures)")
+    p.add_argument("--pc-envs", type=int, default=0, help="profile case: environments of the first group "
+                                                          "(the others scaled alike; 0: the workload's)")
+    p.add_argument("--pc-form", default="batched", choices=["batched", "plain"])
+    p.add_argument("--pc-h", type=int, default=32)
+    p.add_argument("--pc-reps", type=int, default=1)
+    p.add_argument("--pc-tape", type=int, default=0, help="profile case: 1 keeps the window tape (batched)")
+    p.add_argument("--pc-lanes", type=int, default=0)
+    p.add_argument("--pc-warps", type=int, default=0)
     p.add_argument("--h-sweep", default="",
                    help="window-length study instead of the contract line: comma-separated h values; "
                         "N = samples // h environments of the workload's first model (see --samples)")
@@ -235,10 +269,11 @@ def reference_main(args, rank, world):
         return
     wl = I.workload(args.workload)
     n_total = sum(n for _, n in wl.groups)
-    rates = []
-    for _ in range(args.warmup):
-        pass   # the oracle has no warm-up state; W untimed steps are not needed on the CPU
-    samples = []
+    # warm-up: W untimed runs of a small sample (one environment, one step of
+    # each group) load the oracle and touch its code paths
+    for s in range(args.warmup):
+        oracle_workload_rate([(m, 1) for m, _ in wl.groups], seed=1000 + s, target_s=0.0)
+    rates, samples = [], []
     for s in range(args.steps):
         r, threads, dt, desc = oracle_workload_rate(wl.groups, seed=s, target_s=min(12.0, 60.0 / max(1, args.steps)))
         rates.append(r)
@@ -248,12 +283,14 @@ def reference_main(args, rank, world):
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "env-steps/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * n_total * H / value,
+        "ms_per_step_basis": f"extrapolated to the whole workload ({n_total} environments x {H} steps) from the "
+                            f"median rate of the timed samples ({samples[0]} per timed step)",
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": wl.name, "n_envs": n_total, "h": H,
                    "substeps": model.substeps if len(wl.groups) == 1 else [m.substeps for m, _ in wl.groups],
                    "form": "FP64 CPU oracle, forward + dual-number exact adjoint"},
         "cpu_baseline": {"value": value, "unit": "env-steps/s", "cores": threads, "kind": "oracle",
-                         "cpu_model": host_cpu_model(), "sample": f"{samples[0]} per timed step"},
+                         "cpu_model": host_cpu_model(), "sample": f"{samples[0]} per timed step (extrapolated)"},
         "e2e": {"value": value, "unit": "env-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -373,6 +410,67 @@ def shac_main(args):
 
 
 # ------------------------------------------------------------------- GPU ---
+def workload_inputs(sim, groups, seed, h, dev):
+    """Seeded initial state and actions of every group, packed."""
+    import torch
+    from paper_2204_07137_gb300 import inputs as I
+    q0 = sim.pack([I.initial_state(m, n, seed)[0] for m, n in groups], "q")
+    qd0 = sim.pack([I.initial_state(m, n, seed)[1] for m, n in groups], "qd")
+    act = torch.cat([torch.from_numpy(I.window_actions(m, n, h, seed).reshape(h, -1)) for m, n in groups],
+                    dim=1).to(dev).contiguous()
+    return q0, qd0, act
+
+
+class Timer:
+    """CUDA-event timing on one stream: W warm-up runs, then K timed runs, each
+    after an L2 flush; the median of the K per-run times (ms), max over ranks
+    by the caller.  Barrier + synchronize on both sides of the timed region."""
+
+    def __init__(self, stream, flush, dist):
+        self.stream, self.flush, self.dist = stream, flush, dist
+
+    def __call__(self, fn, steps, warmup):
+        import torch
+        with torch.cuda.stream(self.stream):
+            for _ in range(warmup):
+                fn()
+            self.stream.synchronize()
+            if self.dist is not None:
+                self.dist.barrier()
+            torch.cuda.synchronize()
+            ts = []
+            for _ in range(steps):
+                self.flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(self.stream)
+                fn()
+                e1.record(self.stream)
+                e1.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            torch.cuda.synchronize()
+            if self.dist is not None:
+                self.dist.barrier()
+        return statistics.median(ts)
+
+
+def capture_window(sim, q0, qd0, act, rbar, zq, zqd, stream):
+    """Eager forward + adjoint window (outputs allocated), then both captured
+    into one CUDA graph writing the same outputs."""
+    import torch
+    with torch.cuda.stream(stream):
+        outf = sim.window_forward(q0, qd0, act, stream=stream)
+        outa = sim.window_adjoint(outf[0], outf[1], act, rbar, zq, zqd, stream=stream)
+    stream.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(stream):
+        with torch.cuda.graph(graph, stream=stream):
+            sim.window_forward(q0, qd0, act, out=outf, stream=stream)
+            sim.window_adjoint(outf[0], outf[1], act, rbar, zq, zqd, out=outa, stream=stream)
+    stream.synchronize()
+    return graph, outf, outa
+
+
 def gpu_main(args, rank, world, dist):
     import torch
     from paper_2204_07137_gb300 import build, inputs as I
@@ -384,66 +482,47 @@ def gpu_main(args, rank, world, dist):
     wl = I.workload(args.workload)
     groups = wl.groups
     n_envs = wl.n_envs
+    n_sms = torch.cuda.get_device_properties(dev).multi_processor_count
 
     def make(form):
         return Simulator(groups, form=form, h_max=H)
 
-    sim = make("batched")
-    ws_recompute = sim.workspace.numel()
-    sim.set_window_tape(True)   # the forward keeps every substep record; the adjoint reads them back
-    tape_bytes = (sim.workspace.numel() - ws_recompute) / (H * (n_envs + 31 * len(groups)))
     seed = shard_seed(rank)
-    q0 = sim.pack([I.initial_state(m, n, seed)[0] for m, n in groups], "q")
-    qd0 = sim.pack([I.initial_state(m, n, seed)[1] for m, n in groups], "qd")
-    act = torch.cat([torch.from_numpy(I.window_actions(m, n, H, seed).reshape(H, -1)) for m, n in groups],
-                    dim=1).to(dev).contiguous()
+    sim = make("batched")   # the configured variant: per-step checkpoints, substeps recomputed in the adjoint
+    q0, qd0, act = workload_inputs(sim, groups, seed, H, dev)
     # loss = mean reward over the window: reward cotangent 1 / (N h)
     rbar = torch.full((H, n_envs), 1.0 / (n_envs * H), device=dev)
     zq = torch.zeros(H + 1, sim.q_size, device=dev)
     zqd = torch.zeros(H + 1, sim.qd_size, device=dev)
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.Stream(device=dev)
+    timed = Timer(stream, flush, dist)
 
-    # ---- batched form: graph-captured forward + adjoint window
-    with torch.cuda.stream(stream):
-        outf = sim.window_forward(q0, qd0, act, stream=stream)
-        outa = sim.window_adjoint(outf[0], outf[1], act, rbar, zq, zqd, stream=stream)
-    stream.synchronize()
-    graph = torch.cuda.CUDAGraph()
-    with torch.cuda.stream(stream):
-        with torch.cuda.graph(graph, stream=stream):
-            sim.window_forward(q0, qd0, act, out=outf, stream=stream)
-            sim.window_adjoint(outf[0], outf[1], act, rbar, zq, zqd, out=outa, stream=stream)
-    stream.synchronize()
+    # ---- launch shape: the library's measured search on this batch
+    default_shape = [sim.get_launch(g) for g in range(len(groups))]
+    tune = None
+    if args.autotune_ms > 0:
+        g0, _, _ = capture_window(sim, q0, qd0, act, rbar, zq, zqd, stream)
+        ms_default = timed(g0.replay, 5, 2)
+        del g0
+        shape = sim.autotune_native(budget_ms=args.autotune_ms, stream=stream)
+        tune = {"default": {"lanes_per_env": [l for l, _ in default_shape], "warps_per_cta": default_shape[0][1],
+                            "ms_per_window": ms_default},
+                "chosen": {"lanes_per_env": [l for l, _ in shape], "warps_per_cta": shape[0][1]},
+                "search": "coordinate descent over lanes per environment (each group) then warps per CTA, "
+                          f"h = 4 windows from the rest configuration, budget {args.autotune_ms} ms"}
+    shape = [sim.get_launch(g) for g in range(len(groups))]
 
-    def timed(fn, steps, warmup, per_kernel=None):
-        with torch.cuda.stream(stream):
-            for _ in range(warmup):
-                fn()
-            stream.synchronize()
-            if dist is not None:
-                dist.barrier()
-            torch.cuda.synchronize()
-            total = 0.0
-            for _ in range(steps):
-                flush.zero_()
-                e0 = torch.cuda.Event(enable_timing=True)
-                e1 = torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                fn()
-                e1.record(stream)
-                e1.synchronize()
-                total += e0.elapsed_time(e1)
-            torch.cuda.synchronize()
-            if dist is not None:
-                dist.barrier()
-        return total / steps   # ms per step
-
+    # ---- the configured variant: graph-captured forward + recomputing adjoint
+    graph, outf, outa = capture_window(sim, q0, qd0, act, rbar, zq, zqd, stream)
     sampler = ClockSampler(dev.index) if rank == 0 else None
     if sampler:
         sampler.start()
-    ms_batched = timed(graph.replay, args.steps, args.warmup)
+    ms_window = timed(graph.replay, args.steps, args.warmup)
     clocks = sampler.stop() if sampler else None
+    if tune is not None:
+        tune["chosen"]["ms_per_window"] = timed(graph.replay, 5, 1)
+        tune["default"]["note"] = "ms_per_window of each shape: graph replay of the h = 32 window, median of 5"
 
     # per-kernel durations (eager launches, same stream) for the roofline
     def one_fwd():
@@ -452,24 +531,26 @@ def gpu_main(args, rank, world, dist):
     def one_adj():
         sim.window_adjoint(outf[0], outf[1], act, rbar, zq, zqd, out=outa, stream=stream)
 
-    ms_fwd = timed(one_fwd, max(3, args.steps // 2), 1)
-    ms_adj = timed(one_adj, max(3, args.steps // 2), 1)
+    ms_fwd = timed(one_fwd, max(5, args.steps // 2), 1)
+    ms_adj = timed(one_adj, max(5, args.steps // 2), 1)
 
-    # ---- the same window with the recomputing adjoint (no window tape)
-    rsim = make("batched")
-    with torch.cuda.stream(stream):
-        rof = rsim.window_forward(q0, qd0, act, stream=stream)
-        roa = rsim.window_adjoint(rof[0], rof[1], act, rbar, zq, zqd, stream=stream)
-    stream.synchronize()
-    rgraph = torch.cuda.CUDAGraph()
-    with torch.cuda.stream(stream):
-        with torch.cuda.graph(rgraph, stream=stream):
-            rsim.window_forward(q0, qd0, act, out=rof, stream=stream)
-            rsim.window_adjoint(rof[0], rof[1], act, rbar, zq, zqd, out=roa, stream=stream)
-    stream.synchronize()
-    ms_recompute = timed(rgraph.replay, args.steps, args.warmup)
-    same = all(torch.equal(x, y) for x, y in zip(tuple(rof) + tuple(roa), tuple(outf) + tuple(outa)))
-    del rgraph, rsim
+    # ---- the same window with the window tape (every substep record of the
+    # forward kept in HBM; the adjoint reads them instead of recomputing)
+    tsim = make("batched")
+    for g, (l, w) in enumerate(shape):
+        tsim.set_launch(g, l, w)
+    ws_step = tsim.workspace.numel()
+    tsim.set_window_tape(True)
+    tape_bytes = (tsim.workspace.numel() - ws_step) / (H * (n_envs + 31 * len(groups)))
+    tgraph, toutf, touta = capture_window(tsim, q0, qd0, act, rbar, zq, zqd, stream)
+    ms_tape = timed(tgraph.replay, args.steps, args.warmup)
+    ms_tape_adj = timed(lambda: tsim.window_adjoint(toutf[0], toutf[1], act, rbar, zq, zqd, out=touta, stream=stream),
+                        max(5, args.steps // 2), 1)
+    graph.replay()
+    tgraph.replay()
+    torch.cuda.synchronize()
+    same = all(torch.equal(x, y) for x, y in zip(tuple(outf) + tuple(outa), tuple(toutf) + tuple(touta)))
+    del tgraph, tsim
 
     # ---- episodic window (early termination with in-kernel reset, gradient
     # cut at resets), graph captured like the main window: the task heights and
@@ -493,11 +574,14 @@ def gpu_main(args, rank, world, dist):
     stream.synchronize()
     ms_episodic = timed(graph_ep.replay, args.steps, args.warmup)
     done_frac = float(oef[3].float().mean())
+    del graph_ep
 
-    # gradient validity gate: sampled environments against the FP64 oracle
-    grad_rel = None
+    # gradient validity gate: sampled environments of every group against the FP64 oracle
+    graph.replay()
+    torch.cuda.synchronize()
+    grad = None
     if rank == 0 and args.grad_check_envs > 0:
-        grad_rel = gradient_check(sim, groups, outf, outa, act, rbar, n_sample=args.grad_check_envs)
+        grad = gradient_check(sim, groups, outf, outa, act, rbar, n_sample=args.grad_check_envs)
 
     # ---- plain form on the same inputs
     plain = make("plain")
@@ -510,6 +594,7 @@ def gpu_main(args, rank, world, dist):
         plain.window_adjoint(pf[0], pf[1], act, rbar, zq, zqd, out=pa, stream=stream)
 
     ms_plain = timed(plain_step, args.plain_steps, args.warmup)
+    del plain
 
     # ---- end to end through the public API with pinned host buffers
     hq0 = q0.cpu().pin_memory()
@@ -537,76 +622,102 @@ def gpu_main(args, rank, world, dist):
     d2h = 4 * (hrew.numel() + hab.numel() + hq0b.numel() + hqd0b.numel())
 
     # max over ranks
-    ms_batched, ms_plain, ms_e2e, ms_fwd, ms_adj, ms_episodic, ms_recompute = max_over_ranks(
-        [ms_batched, ms_plain, ms_e2e, ms_fwd, ms_adj, ms_episodic, ms_recompute], dist, dev)
+    ms_window, ms_plain, ms_e2e, ms_fwd, ms_adj, ms_episodic, ms_tape, ms_tape_adj = max_over_ranks(
+        [ms_window, ms_plain, ms_e2e, ms_fwd, ms_adj, ms_episodic, ms_tape, ms_tape_adj], dist, dev)
     if rank != 0:
         return
     env_steps = n_envs * H * world
-    value = env_steps / (ms_batched * 1e-3)
+    value = env_steps / (ms_window * 1e-3)
     plain_value = env_steps / (ms_plain * 1e-3)
-    dominant, ms_dom = ("k_batched_adjoint", ms_adj) if ms_adj >= ms_fwd else ("k_batched_forward", ms_fwd)
-    counts = ALGO_FLOPS_PER_ENV_STEP.get(wl.name)
-    af = counts["adjoint" if dominant.endswith("adjoint") else "forward"] if counts else None
-    achieved = None if af is None else af * n_envs * H / (ms_dom * 1e-3) / 1e12
-    traffic = TRAFFIC_BYTES_PER_LAUNCH.get(wl.name, {}).get(dominant)
+    sm_max = (clocks or {}).get("sm_max_mhz") or DEFAULT_SM_MAX_MHZ
+    sm_med = (clocks or {}).get("sm_mhz") or sm_max
+    peak = fp32_peak_tflops(n_sms, sm_max)
+    peak_src = (f"derived FP32 peak: {n_sms} SMs (device query) x {FP32_LANES_PER_SM} lanes x "
+                f"{FLOPS_PER_LANE_CYCLE} flop x {sm_max:.0f} MHz (maximum SM clock sampled)")
+    model0 = groups[0][0]
+    counts = FLOPS_PER_ENV_STEP.get(model0.name) if len(groups) == 1 else None
+    bytes_alg = algo_bytes_per_env_step(model0) if len(groups) == 1 else None
+    per_launch = n_envs * H
+    dominant, ms_dom = ("adjoint", ms_adj) if ms_adj >= ms_fwd else ("forward", ms_fwd)
+    dom_flops = None
+    if counts:
+        dom_flops = counts["recompute"] + counts["reverse"] if dominant == "adjoint" else counts["forward"]
+    achieved = None if dom_flops is None else dom_flops * per_launch / (ms_dom * 1e-3) / 1e12
+    traffic = TRAFFIC_BYTES_PER_LAUNCH.get(wl.name, {}).get("adjoint_recompute" if dominant == "adjoint"
+                                                             else "forward")
     hbm_peak, hbm_src = measured_hbm_gbs()
-    hbm_bytes = traffic if traffic is not None else \
-        (ALGO_BYTES_PER_ENV_STEP.get(dominant, 0) + tape_bytes) * n_envs * H
-    hbm_gbs = hbm_bytes / (ms_dom * 1e-3) / 1e9
-    # the window's algorithmic work (forward + reverse) over each form's window
-    # time: the same numerator for both forms, whatever each recomputes
-    wf = None if counts is None else counts["forward"] + counts["adjoint"]
+    dom_bytes = None if bytes_alg is None else bytes_alg[dominant] * per_launch
+    # the window's work (forward + recompute + reverse) over each form's window time
+    wf = None if counts is None else counts["forward"] + counts["recompute"] + counts["reverse"]
 
-    def window_roofline(ms):
-        if wf is None:
+    def window_roofline(ms, flops_per_env_step):
+        if flops_per_env_step is None:
             return None
-        a = wf * env_steps / (ms * 1e-3) / 1e12
-        return {"bound": "alu", "achieved": a, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": a / FP32_PEAK_TFLOPS, "algo_flops_per_env_step": wf,
-                "peak_source": "derived FP32 peak: 152 SMs x 128 lanes x 2 x 2.07 GHz"}
+        a = flops_per_env_step * env_steps / (ms * 1e-3) / 1e12
+        return {"bound": "alu", "achieved": a, "peak": peak, "unit": "TFLOP/s", "frac": a / peak,
+                "flops_per_env_step": flops_per_env_step, "peak_source": peak_src}
 
     line = {
         "metric": METRIC, "value": value, "unit": "env-steps/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_batched, "higher_is_better": True, "scaling": "weak",
+        "warmup": args.warmup, "ms_per_step": ms_window, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": wl.name, "n_envs_per_gpu": n_envs, "h": H,
-                   "substeps": groups[0][0].substeps if len(groups) == 1 else [m.substeps for m, _ in groups],
-                   "form": "batched, forward+adjoint captured in one CUDA graph, window tape kept in HBM",
-                   "tape_bytes_per_env_step": tape_bytes,
-                   "lanes_per_env": [sim.get_launch(g)[0] for g in range(len(groups))],
-                   "warps_per_cta": sim.get_launch(0)[1], "l2": "flushed (256 MB write) before each timed step",
+                   "substeps": model0.substeps if len(groups) == 1 else [m.substeps for m, _ in groups],
+                   "form": "batched; per-control-step checkpoints, substeps recomputed in the adjoint; forward + "
+                           "adjoint captured in one CUDA graph",
+                   "lanes_per_env": [l for l, _ in shape], "warps_per_cta": shape[0][1],
+                   "timing": "median of the timed steps", "l2": "flushed (256 MB write) before each timed step",
                    "parallelism": f"env-sharded replicas x{world}"},
+        "autotune": tune,
         "plain_form": {"value": plain_value, "unit": "env-steps/s", "ms_per_step": ms_plain,
-                       "steps": args.plain_steps, "window_roofline": window_roofline(ms_plain)},
-        "window_roofline": window_roofline(ms_batched),
+                       "steps": args.plain_steps, "window_roofline": window_roofline(ms_plain, wf)},
+        "window_roofline": window_roofline(ms_window, wf),
         "speedup_vs_plain": value / plain_value,
-        "recompute_window": {"value": env_steps / (ms_recompute * 1e-3), "unit": "env-steps/s",
-                             "ms_per_step": ms_recompute, "bitwise_equal_to_taped": bool(same),
-                             "note": "adjoint recomputes each step's substeps instead of reading the window tape"},
+        "window_tape": {"value": env_steps / (ms_tape * 1e-3), "unit": "env-steps/s", "ms_per_step": ms_tape,
+                        "bitwise_equal_to_recompute": bool(same),
+                        "tape_bytes_per_env_step": tape_bytes,
+                        "workspace_bytes": int(ws_step + tape_bytes * H * (n_envs + 31 * len(groups))),
+                        "ms_adjoint_kernel": ms_tape_adj,
+                        "window_roofline": window_roofline(ms_tape, None if counts is None else
+                                                           counts["forward"] + counts["reverse"]),
+                        "scratch_vs_algorithmic_bytes": None if bytes_alg is None else
+                        (tape_bytes + bytes_alg["adjoint"]) / bytes_alg["adjoint"],
+                        "note": "the forward keeps every substep record in HBM and the adjoint reads them back "
+                                "instead of recomputing each step's substeps; same results bit for bit"},
         "episodic": {"value": env_steps / (ms_episodic * 1e-3), "unit": "env-steps/s", "ms_per_step": ms_episodic,
                      "done_frac": done_frac,
                      "rule": "root below the task height or the task horizon; seeded reset states; "
                              "forward + adjoint with the gradient cut at resets, one CUDA graph"},
-        "kernels_ms": {"k_batched_forward": ms_fwd, "k_batched_adjoint": ms_adj},
-        "grad_rel_err_max": grad_rel,
+        "kernels_ms": {"k_batched_forward": ms_fwd, "k_batched_adjoint (recompute)": ms_adj},
+        "grad_rel_err": grad,
         "gpu_launches": 2 * args.steps,
         "clocks": clocks,
         "e2e": {"value": env_steps / (ms_e2e * 1e-3), "unit": "env-steps/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
-        "roofline": {"bound": "alu", "kernel": dominant, "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
-                     "unit": "TFLOP/s", "frac": None if achieved is None else achieved / FP32_PEAK_TFLOPS,
-                     "peak_source": "derived FP32 peak: 152 SMs x 128 lanes x 2 x 2.07 GHz",
-                     "traffic": traffic, "algo_flops_per_env_step": af,
-                     "algo_bytes_per_env_step": ALGO_BYTES_PER_ENV_STEP.get(dominant, 0) + tape_bytes,
-                     "hbm": {"achieved": hbm_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": hbm_gbs / hbm_peak,
-                             "bytes": "ncu traffic" if traffic is not None else "algorithmic",
-                             "peak_source": hbm_src}},
+        "roofline": {"bound": "alu", "kernel": f"k_batched<{1 if dominant == 'adjoint' else 0}> ({dominant}"
+                                               f"{', recomputing' if dominant == 'adjoint' else ''})",
+                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": None if achieved is None else achieved / peak,
+                     "frac_at_median_clock": None if achieved is None else
+                     achieved / fp32_peak_tflops(n_sms, sm_med),
+                     "peak_source": peak_src, "traffic": traffic,
+                     "flops_per_env_step": dom_flops,
+                     "flops_source": "FP32 work the one-environment-per-thread form executes for the same "
+                                     "stages (ncu count of FADD + FMUL + 2 FFMA)",
+                     "units_per_launch": per_launch,
+                     "hbm": None if dom_bytes is None else
+                     {"achieved": dom_bytes / (ms_dom * 1e-3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                      "frac": dom_bytes / (ms_dom * 1e-3) / 1e9 / hbm_peak,
+                      "algo_bytes_per_env_step": bytes_alg[dominant],
+                      "algo_bytes_total_per_env_step": bytes_alg["forward"] + bytes_alg["adjoint"],
+                      "peak_source": hbm_src}},
     }
     if not args.no_cpu_baseline:
         r, threads, dt, desc = oracle_workload_rate(groups, seed=0, target_s=12.0)
         line["cpu_baseline"] = {"value": r, "unit": "env-steps/s", "cores": threads, "kind": "oracle",
                                 "cpu_model": host_cpu_model(),
-                                "sample": f"{desc}, forward + exact adjoint, {dt:.1f} s",
+                                "sample": f"{desc}, forward + exact adjoint, {dt:.1f} s; rate extrapolated to the "
+                                          f"workload",
                                 "single_core": oracle_single_core_rate(args.workload)}
     print(json.dumps(line), flush=True)
 
@@ -628,27 +739,62 @@ def oracle_single_core_rate(workload: str):
 
 
 def gradient_check(sim, groups, outf, outa, act, rbar, n_sample: int = 4):
-    """Max per-env relative error of the window gradients (action and
-    initial-state cotangents) on sampled environments vs the FP64 oracle
-    adjoint run on the GPU checkpoints."""
+    """Per group: the maximum over sampled environments of the per-environment
+    relative error (2-norm) of the window gradients (action and initial-state
+    cotangents) against the FP64 oracle adjoint run on the GPU checkpoints."""
     from oracle import oracle
-    model, N = groups[0]
-    o = oracle.Oracle(model)
-    rng = np.random.default_rng(0)
-    envs = np.sort(rng.choice(N, size=min(n_sample, N), replace=False))
-    qt = sim.unpack(outf[0], "q")[0][:, :, envs]
-    qdt = sim.unpack(outf[1], "qd")[0][:, :, envs]
-    a = sim.unpack(act, "act")[0][:, :, envs]
-    rb = rbar.cpu().numpy()[:, envs]            # group 0 comes first in the reward block
-    qb, qdb, ab = o.window_adjoint(qt.transpose(0, 2, 1), qdt.transpose(0, 2, 1), a.transpose(0, 2, 1), rb,
-                                   np.zeros((len(envs), model.nq)), np.zeros((len(envs), model.nv)))
-    g_a = sim.unpack(outa[2], "act")[0][:, :, envs].transpose(2, 0, 1).reshape(len(envs), -1)
-    g_q = sim.unpack(outa[0], "q")[0][:, envs].T
-    g_qd = sim.unpack(outa[1], "qd")[0][:, envs].T
-    got = np.concatenate([g_a, g_q, g_qd], axis=1)
-    ref = np.concatenate([ab.transpose(1, 0, 2).reshape(len(envs), -1), qb, qdb], axis=1)
-    rel = np.linalg.norm(got - ref, axis=1) / np.linalg.norm(ref, axis=1)
-    return float(rel.max())
+    qt_all, qdt_all = sim.unpack(outf[0], "q"), sim.unpack(outf[1], "qd")
+    a_all = sim.unpack(act, "act")
+    ga_all, gq_all, gqd_all = sim.unpack(outa[2], "act"), sim.unpack(outa[0], "q"), sim.unpack(outa[1], "qd")
+    rb_all = rbar.cpu().numpy()
+    out, off = {}, 0
+    for gi, (model, N) in enumerate(groups):
+        o = oracle.Oracle(model)
+        envs = np.sort(np.random.default_rng(gi).choice(N, size=min(n_sample, N), replace=False))
+        qt = qt_all[gi][:, :, envs]
+        qdt = qdt_all[gi][:, :, envs]
+        a = a_all[gi][:, :, envs]
+        rb = rb_all[:, off + envs]
+        qb, qdb, ab = o.window_adjoint(qt.transpose(0, 2, 1), qdt.transpose(0, 2, 1), a.transpose(0, 2, 1), rb,
+                                       np.zeros((len(envs), model.nq)), np.zeros((len(envs), model.nv)))
+        g_a = ga_all[gi][:, :, envs].transpose(2, 0, 1).reshape(len(envs), -1)
+        got = np.concatenate([g_a, gq_all[gi][:, envs].T, gqd_all[gi][:, envs].T], axis=1)
+        ref = np.concatenate([ab.transpose(1, 0, 2).reshape(len(envs), -1), qb, qdb], axis=1)
+        rel = np.linalg.norm(got - ref, axis=1) / np.linalg.norm(ref, axis=1)
+        out[f"{gi}:{model.name}"] = {"max": float(rel.max()), "envs": envs.tolist(), "rel": rel.tolist()}
+        off += N
+    return out
+
+
+def profile_case_main(args):
+    """A few windows of a workload through the public API, no timing and no
+    checks, for profiler captures (the ncu commands recorded with the kernel
+    summaries): --pc-envs environments of the first group (the others scaled
+    alike), --pc-form, --pc-h steps, --pc-reps windows, --pc-tape, --pc-lanes /
+    --pc-warps (0: the library's default shape)."""
+    import torch
+    from paper_2204_07137_gb300 import build, inputs as I
+    from paper_2204_07137_gb300.sim import Simulator
+    build.build()
+    wl = I.workload(args.workload)
+    scale = args.pc_envs / wl.groups[0][1] if args.pc_envs > 0 else 1.0
+    groups = [(m, max(1, int(round(n * scale)))) for m, n in wl.groups]
+    h = args.pc_h
+    sim = Simulator(groups, form=args.pc_form, h_max=h)
+    if args.pc_lanes or args.pc_warps:
+        sim.set_launch(-1, args.pc_lanes, args.pc_warps)
+    if args.pc_form == "batched" and args.pc_tape:
+        sim.set_window_tape(True)
+    dev = sim.device
+    q0, qd0, act = workload_inputs(sim, groups, 0, h, dev)
+    rb = torch.ones(h, sim.n_envs, device=dev)
+    zq = torch.zeros(h + 1, sim.q_size, device=dev)
+    zqd = torch.zeros(h + 1, sim.qd_size, device=dev)
+    for _ in range(args.pc_reps):
+        f = sim.window_forward(q0, qd0, act)
+        sim.window_adjoint(f[0], f[1], act, rb, zq, zqd)
+    torch.cuda.synchronize()
+    assert bool(torch.isfinite(f[0]).all())
 
 
 def main():
@@ -667,6 +813,9 @@ def main():
     try:
         if args.impl == "reference":
             reference_main(args, rank, world)
+        elif args.profile_case:
+            if rank == 0:
+                profile_case_main(args)
         elif args.h_sweep:
             if rank == 0:
                 h_sweep_main(args)

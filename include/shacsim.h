@@ -149,20 +149,35 @@ void shac_model_destroy(shac_model* model);
 void shac_model_dims(const shac_model* model, int32_t* nq, int32_t* nv, int32_t* na);
 
 /* A batch of n_groups articulation groups (models[g] with n_envs[g] >= 0
- * environments each) executed in one form.  Uploads the model constants to
- * the current CUDA device (the one allocation point).  window_h_max bounds the
- * h accepted by the window calls. */
+ * environments each) executed in one form (Sec. 3.1: the simulator runs the
+ * environments in parallel on the GPU, the dense routines and the contact and
+ * joint forces of every environment at once).  Environments of a batch are
+ * independent.  Uploads the model constants and the work-item table to the
+ * current CUDA device, which the batch stays bound to (the one allocation
+ * point).  window_h_max bounds the h accepted by the window calls.  Errors:
+ * SHAC_ERR_INVALID_ARG (null pointers, n_groups outside 1..8, a negative
+ * count, an unknown form, window_h_max < 1); SHAC_ERR_CUDA. */
 shac_status shac_batch_create(const shac_model* const* models, const int32_t* n_envs, int32_t n_groups,
                               int32_t form, int32_t window_h_max, shac_batch** out);
 void shac_batch_destroy(shac_batch* batch);
 /* Totals over groups: sum nq_g N_g, sum nv_g N_g, sum na_g N_g, sum N_g. */
 void shac_batch_dims(const shac_batch* batch, int64_t* q_size, int64_t* qd_size, int64_t* act_size,
                      int64_t* n_envs);
-/* Bytes of caller-allocated device workspace the batch needs (256-byte aligned pointer). */
+/* Bytes of caller-allocated device workspace the batch needs (the caller
+ * passes a 256-byte aligned pointer to every step and window call).  It holds
+ * the scratch of one control step for every environment: the per-substep
+ * records that Sec. 3.1 keeps for the backward pass (link poses, inertias,
+ * contact items, the Cholesky factor) and, with the window tape, those of
+ * every step of a window.  0 for a null batch. */
 size_t shac_batch_workspace_bytes(const shac_batch* batch);
 
-/* One control step (K substeps, then the reward).  q/qd/act: [q_size]/[qd_size]/[act_size];
- * q_next/qd_next likewise; reward: [n_envs].  Inputs and outputs must not alias. */
+/* One control step s_{t+1} = F(s_t, a_t) (Sec. 3.1): K substeps with the
+ * action held, each solving Eq. fwd_dynamics for the joint accelerations (CRBA
+ * mass matrix, Cholesky factorisation) and taking a semi-implicit Euler step;
+ * then the reward on the post-step state.  q/qd/act: [q_size]/[qd_size]/
+ * [act_size] device arrays; q_next/qd_next likewise; reward: [n_envs].
+ * Inputs and outputs must not alias.  Errors: SHAC_ERR_INVALID_ARG (null
+ * pointer, unaligned workspace), SHAC_ERR_CUDA (launch failure). */
 shac_status shac_step(shac_batch* batch, void* stream, void* workspace,
                       const float* q, const float* qd, const float* act,
                       float* q_next, float* qd_next, float* reward);
@@ -246,14 +261,20 @@ shac_status shac_window_adjoint_episodic(shac_batch* batch, void* stream, void* 
  * Same arguments and results as shac_step_adjoint minus the workspace: the
  * scratch (work counter and substep records) lives in a 64 MiB device array
  * compiled into the library, resident on every GPU that loads it until the
- * process exits.  Nothing is allocated by the call.  A batch whose
- * shac_batch_workspace_bytes exceeds 64 MiB is rejected with
- * SHAC_ERR_CAPACITY (for the ant-like model: up to about 1500 environments).
- * The first call on a device looks up the array's device address with that
- * device current; make that first call before any stream capture.  Every call
- * on a device shares the one array, and it keeps the last call's contents:
- * calls that may overlap on the GPU (different streams, or concurrent host
- * threads) race on it and must be serialised by the caller. */
+ * process exits.  Nothing is allocated by the call.  A batch whose step-level
+ * scratch exceeds 64 MiB is rejected with SHAC_ERR_CAPACITY: that is what
+ * shac_batch_workspace_bytes reports with the window tape off (for the
+ * ant-like model: up to about 1500 environments); the window tape's share is
+ * never used by step calls, so turning the tape on does not change the limit.
+ * The current device must be the one the batch was created on
+ * (SHAC_ERR_INVALID_ARG otherwise, nothing launched).  The first call on a
+ * device looks up the array's device address with that device current and
+ * keeps it for the life of the process; make that first call before any
+ * stream capture, and do not use the library across a device reset.  Every
+ * call on a device shares the one array, and it keeps the last call's
+ * contents (the work counter is cleared by each call): calls that may overlap
+ * on the GPU (different streams, or concurrent host threads) race on it and
+ * must be serialised by the caller. */
 shac_status shac_step_adjoint_static(shac_batch* batch, void* stream,
                                      const float* q, const float* qd, const float* act,
                                      const float* q_next_bar, const float* qd_next_bar, const float* reward_bar,
@@ -275,16 +296,20 @@ shac_status shac_batch_get_launch(const shac_batch* batch, int32_t group, int32_
  * warm-up, best of two), from the rest configuration (joint coordinates 0,
  * free joints at the origin with the identity orientation, zero velocities and
  * actions).  The fastest shape is applied to the batch (as
- * shac_batch_set_launch would) and kept.  `workspace`: the caller's workspace
- * of shac_batch_workspace_bytes (256-byte aligned), overwritten.  budget_ms:
- * wall-clock limit of the search (> 0; the best shape found so far is kept
- * when it runs out).  Synchronises the stream and allocates and frees
- * temporary device buffers for the inputs and outputs of the timed windows, so
- * it must not be called during a stream capture.  A PLAIN batch, or one with
- * no environment, returns SHAC_OK unchanged.  Errors: SHAC_ERR_INVALID_ARG for
- * a null batch, an unaligned workspace or budget_ms <= 0; SHAC_ERR_CUDA if a
- * CUDA call fails (the launch shape is then left as it was). */
+ * shac_batch_set_launch would) and kept.  `workspace`: a caller buffer of
+ * shac_autotune_workspace_bytes (256-byte aligned), overwritten: the batch's
+ * workspace followed by the inputs and outputs of the timed windows; the call
+ * allocates no device memory.  budget_ms: wall-clock limit of the search
+ * (> 0; the best shape found so far is kept when it runs out).  Synchronises
+ * the stream, so it must not be called during a stream capture.  A PLAIN
+ * batch, or one with no environment, returns SHAC_OK unchanged.  Errors:
+ * SHAC_ERR_INVALID_ARG for a null batch, an unaligned workspace or
+ * budget_ms <= 0; SHAC_ERR_CUDA if a CUDA call fails (the launch shape is then
+ * left as it was). */
 shac_status shac_autotune(shac_batch* batch, void* stream, void* workspace, int32_t budget_ms);
+/* Bytes of the workspace shac_autotune needs (shac_batch_workspace_bytes plus
+ * the timed windows' buffers). */
+size_t shac_autotune_workspace_bytes(const shac_batch* batch);
 
 /* Window tape (BATCHED form; SHAC_ERR_UNSUPPORTED for PLAIN): keep = 1 makes
  * shac_window_forward (and its episodic variant) store every substep record of

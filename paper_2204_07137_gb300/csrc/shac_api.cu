@@ -42,6 +42,7 @@ struct shac_batch {
   unsigned int* d_flags = nullptr;
   WorkItem* d_items = nullptr;
   int n_items = 0;
+  int64_t items_cap = 0;   // capacity of d_items (sum of N_g: one environment per item)
   int device = 0, num_sms = 0;
   // workspace layout (bytes)
   size_t ws_counter = 0, ws_tape = 0, ws_plain = 0, ws_total = 0;
@@ -380,10 +381,11 @@ static shac_status build_items(shac_batch* b) {
   std::stable_sort(items.begin(), items.end(), [](const auto& a, const auto& c) { return a.first > c.first; });
   std::vector<WorkItem> h;
   for (auto& p : items) h.push_back(p.second);
-  if (b->d_items) { cudaFree(b->d_items); b->d_items = nullptr; }
+  // the item buffer is allocated once, in shac_batch_create, for the largest
+  // item count (one environment per item)
+  if ((int64_t)h.size() > b->items_cap) return SHAC_ERR_CAPACITY;
   b->n_items = (int)h.size();
   if (h.empty()) return SHAC_OK;
-  if (cudaMalloc(&b->d_items, h.size() * sizeof(WorkItem)) != cudaSuccess) return SHAC_ERR_CUDA;
   return cuda_ok(cudaMemcpy(b->d_items, h.data(), h.size() * sizeof(WorkItem), cudaMemcpyHostToDevice));
 }
 
@@ -463,6 +465,11 @@ extern "C" shac_status shac_batch_create(const shac_model* const* models, const 
       cudaMemcpy(b->d_models, dm.data(), dm.size() * sizeof(DevModel), cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMalloc(&b->d_flags, sizeof(unsigned int)) != cudaSuccess ||
       cudaMemset(b->d_flags, 0, sizeof(unsigned int)) != cudaSuccess) {
+    shac_batch_destroy(b);
+    return SHAC_ERR_CUDA;
+  }
+  b->items_cap = std::max<int64_t>(1, b->n_envs);
+  if (cudaMalloc(&b->d_items, (size_t)b->items_cap * sizeof(WorkItem)) != cudaSuccess) {
     shac_batch_destroy(b);
     return SHAC_ERR_CUDA;
   }
@@ -769,11 +776,12 @@ constexpr int STATIC_MAX_DEVICES = 64;
 static std::mutex g_static_mutex;
 static void* g_static_addr[STATIC_MAX_DEVICES] = {};
 
-// Device address of the array on the current device, looked up once per device
-// (on the first call made with that device current).
-static shac_status static_scratch_address(void** out) {
-  int dev = -1;
-  if (cudaGetDevice(&dev) != cudaSuccess) return SHAC_ERR_CUDA;
+// Device address of the array on device `dev`, which must be the current
+// device: looked up once per device (on the first call made with that device
+// current) and cached for the life of the process.  A device reset
+// (cudaDeviceReset) reloads the module, possibly at another address, so the
+// library must not be used across one.
+static shac_status static_scratch_address(int dev, void** out) {
   if (dev < 0 || dev >= STATIC_MAX_DEVICES) return SHAC_ERR_UNSUPPORTED;
   std::lock_guard<std::mutex> lock(g_static_mutex);
   if (!g_static_addr[dev]) {
@@ -792,8 +800,13 @@ extern "C" shac_status shac_step_adjoint_static(shac_batch* b, void* stream, con
   if (!b || !q || !qd || !act || !q_next_bar || !qd_next_bar || !reward_bar || !q_bar || !qd_bar || !act_bar)
     return SHAC_ERR_INVALID_ARG;
   if (b->ws_step > STATIC_SCRATCH_BYTES) return SHAC_ERR_CAPACITY;
+  // the array used is the current device's: it must be the GPU that holds the
+  // batch's model tables and work items
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return SHAC_ERR_CUDA;
+  if (dev != b->device) return SHAC_ERR_INVALID_ARG;
   void* ws = nullptr;
-  const shac_status st = static_scratch_address(&ws);
+  const shac_status st = static_scratch_address(dev, &ws);
   if (st != SHAC_OK) return st;
   return run_adjoint(b, (cudaStream_t)stream, ws, 1, q, qd, act, reward_bar, nullptr, nullptr, q_next_bar, qd_next_bar,
                      q_bar, qd_bar, act_bar);
@@ -825,6 +838,29 @@ extern "C" const char* shac_status_string(shac_status s) {
 }
 
 // -------------------------------------------------------------- autotune --
+// Inputs and outputs of the autotuner's timed windows (h = min(h_max, 4)
+// steps), carved from the caller's workspace after the batch's own part.
+static const int AUTOTUNE_MAX_H = 4;
+
+static size_t autotune_parts(const shac_batch* b, size_t* parts) {
+  const size_t h = (size_t)std::min(b->h_max, AUTOTUNE_MAX_H);
+  const size_t nq = (size_t)b->q_size, nqd = (size_t)b->qd_size, na = (size_t)b->act_size, ne = (size_t)b->n_envs;
+  const size_t p[12] = {nq, nqd, h * na, (h + 1) * nq, (h + 1) * nqd, h * ne, h * ne, (h + 1) * nq,
+                        (h + 1) * nqd, nq, nqd, h * na};
+  size_t total = 0;
+  for (int k = 0; k < 12; ++k) {
+    parts[k] = (p[k] + 63) / 64 * 64;   // 256-byte aligned pieces
+    total += parts[k];
+  }
+  return total * sizeof(float);
+}
+
+extern "C" size_t shac_autotune_workspace_bytes(const shac_batch* b) {
+  if (!b) return 0;
+  size_t parts[12];
+  return b->ws_total + autotune_parts(b, parts);
+}
+
 extern "C" shac_status shac_autotune(shac_batch* b, void* stream, void* ws, int32_t budget_ms) {
   if (!b || !aligned_ws(b, ws) || budget_ms <= 0) return SHAC_ERR_INVALID_ARG;
   if (b->form != SHAC_FORM_BATCHED || b->n_items == 0) return SHAC_OK;
@@ -833,19 +869,17 @@ extern "C" shac_status shac_autotune(shac_batch* b, void* stream, void* ws, int3
     return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count() > budget_ms;
   };
   cudaStream_t s = (cudaStream_t)stream;
-  const int h = std::min(b->h_max, 4);
-  // inputs and outputs of the timed windows, in one temporary allocation
-  const size_t nq = (size_t)b->q_size, nqd = (size_t)b->qd_size, na = (size_t)b->act_size, ne = (size_t)b->n_envs;
-  const size_t parts[] = {nq, nqd, h * na, (h + 1) * nq, (h + 1) * nqd, h * ne, h * ne, (h + 1) * nq,
-                          (h + 1) * nqd, nq, nqd, h * na};
-  size_t total = 0;
-  for (size_t p : parts) total += (p + 63) / 64 * 64;
-  float* buf = nullptr;
-  if (cudaMalloc(&buf, total * sizeof(float)) != cudaSuccess) return SHAC_ERR_CUDA;
+  const int h = std::min(b->h_max, AUTOTUNE_MAX_H);
+  const size_t nq = (size_t)b->q_size, nqd = (size_t)b->qd_size;
+  size_t parts[12];
+  const size_t buf_bytes = autotune_parts(b, parts);
+  // the timed windows' buffers follow the batch's workspace (the launch shape
+  // does not change its size)
+  float* buf = reinterpret_cast<float*>(static_cast<char*>(ws) + b->ws_total);
   float* ptr[12];
   {
     size_t off = 0;
-    for (int k = 0; k < 12; ++k) { ptr[k] = buf + off; off += (parts[k] + 63) / 64 * 64; }
+    for (int k = 0; k < 12; ++k) { ptr[k] = buf + off; off += parts[k]; }
   }
   float *q0 = ptr[0], *qd0 = ptr[1], *act = ptr[2], *qt = ptr[3], *qdt = ptr[4], *rew = ptr[5], *rbar = ptr[6];
   float *qtb = ptr[7], *qdtb = ptr[8], *q0b = ptr[9], *qd0b = ptr[10], *actb = ptr[11];
@@ -858,8 +892,9 @@ extern "C" shac_status shac_autotune(shac_batch* b, void* stream, void* ws, int3
         for (int e = 0; e < g.N; ++e) qh[(size_t)b->io.g[gi].q_off + (size_t)(g.m->qs[i] + 6) * g.N + e] = 1.f;
   }
   cudaEvent_t e0 = nullptr, e1 = nullptr;
-  shac_status st = cuda_ok(cudaMemsetAsync(buf, 0, total * sizeof(float), s));
+  shac_status st = cuda_ok(cudaMemsetAsync(buf, 0, buf_bytes, s));
   if (st == SHAC_OK) st = cuda_ok(cudaMemcpyAsync(q0, qh.data(), nq * sizeof(float), cudaMemcpyHostToDevice, s));
+  if (st == SHAC_OK) st = cuda_ok(cudaStreamSynchronize(s));   // qh is a host temporary
   if (st == SHAC_OK) st = cuda_ok(cudaEventCreate(&e0));
   if (st == SHAC_OK) st = cuda_ok(cudaEventCreate(&e1));
   auto window = [&]() -> shac_status {
@@ -923,7 +958,6 @@ extern "C" shac_status shac_autotune(shac_batch* b, void* stream, void* ws, int3
   cudaStreamSynchronize(s);
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
-  cudaFree(buf);
   if (st != SHAC_OK) return st;
   return st_items;
 }

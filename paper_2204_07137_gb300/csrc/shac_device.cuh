@@ -1,11 +1,13 @@
 // Per-environment simulator stages and their adjoints (FP32, sm_103a).
 //
 // The simulator step F (paper Sec. 3.1) is evaluated with spatial (6-D)
-// vectors expressed in world coordinates at the world origin (Plücker
-// coordinates, angular part first): with that choice the motion subspaces,
-// spatial inertias and forces of all links live in one frame, so the
-// composite-rigid-body mass matrix needs no frame transforms and the
-// Newton-Euler recursion is a plain sum along the tree.
+// vectors expressed in world-aligned coordinates about one reference point
+// (Plücker coordinates, angular part first): the world origin for a model
+// without a free root, the free root's origin otherwise (the dynamics are
+// translation invariant; the contact depth adds the root height back).  With
+// that choice the motion subspaces, spatial inertias and forces of all links
+// live in one frame, so the composite-rigid-body mass matrix needs no frame
+// transforms and the Newton-Euler recursion is a plain sum along the tree.
 //
 //   forward dynamics (Eq. fwd_dynamics):  (M + diag(armature)) qdd = tau_j - C(q, qd)
 //   C = ID(q, qd, 0) with gravity as a base acceleration and the external

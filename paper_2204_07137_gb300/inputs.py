@@ -343,7 +343,7 @@ def cartpole(substeps: int = 4) -> ArticulationModel:
                     rw_q=[0.1, 1.0], reward_coef=_loco_coef(0, 0, 0, 0, 0, -BIG, BIG, 0, 0, 0))
 
 
-ANT_DENSITY = 5.0 * 200.0   # "density 5 kg/m^3 scaled": scale 200 (reading, see DESIGN)
+ANT_DENSITY = 5.0 * 200.0   # "density 5 kg/m^3 scaled": scale 200, so that explicit contact damping stays stable
 ANT_FOOT_PENETRATION = 0.002
 
 

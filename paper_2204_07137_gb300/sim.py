@@ -78,9 +78,15 @@ class Simulator:
         """The library's own measured launch-shape search (shac_autotune):
         lanes per environment for each group, then warps per CTA, timed as short
         windows from the rest configuration; the fastest shape stays applied.
-        Synchronises; not for a stream capture."""
-        _lib.check(_lib.load().shac_autotune(self.batch, self._stream(stream), self._ws(), int(budget_ms)),
+        The search's buffers are a temporary torch allocation of
+        shac_autotune_workspace_bytes.  Synchronises; not for a stream capture."""
+        L = _lib.load()
+        nbytes = int(L.shac_autotune_workspace_bytes(self.batch))
+        tmp = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=self.device)
+        assert tmp.data_ptr() % 256 == 0
+        _lib.check(L.shac_autotune(self.batch, self._stream(stream), ctypes.c_void_p(tmp.data_ptr()), int(budget_ms)),
                    "shac_autotune")
+        del tmp
         self._alloc_workspace()
         return [self.get_launch(g) for g in range(len(self.groups))]
 

@@ -55,47 +55,46 @@ def test_every_cta_size_launches_in_a_fresh_context():
     assert out.stdout.strip().endswith("ok")
 
 
-def test_autotune_picks_a_valid_shape():
-    """The launch-shape tuner measures candidate team sizes and CTA sizes on a
-    heterogeneous batch, leaves the batch on a valid shape, and that shape
-    gives the same window up to FP32 reassociation inside a team."""
-    import numpy as np
-    from paper_2204_07137_gb300 import autotune, inputs as I
-    from paper_2204_07137_gb300.sim import Simulator
-    groups = [(I.cartpole(), 40), (I.ant(), 13)]
-    tuned = Simulator(groups, form="batched", h_max=2)
-    ref = Simulator(groups, form="batched", h_max=2)
-    r = autotune.autotune(tuned, h=2, reps=1)
-    assert all(l in autotune.LANES for l in r["lanes"]) and r["warps"] in autotune.WARPS
-    assert np.isfinite(r["ms_window_h"])
-    assert [tuned.get_launch(g)[0] for g in range(2)] == r["lanes"]
-    x = autotune._Inputs(ref, 2)
-    a = tuned.window_forward(x.q0, x.qd0, x.act)
-    b = ref.window_forward(x.q0, x.qd0, x.act)
-    torch.cuda.synchronize()
-    for u, v in zip(a, b):
-        np.testing.assert_allclose(u.cpu().numpy(), v.cpu().numpy(), rtol=1e-4, atol=1e-3)
+LANES = (1, 2, 4, 8, 16, 32)
+WARPS = (1, 2, 4, 8)
 
 
-def test_native_autotune_keeps_a_valid_shape():
-    """shac_autotune (the library's own search) on a heterogeneous batch with
-    the window tape: a valid shape is left applied, the windows it times do not
-    disturb the caller's buffers, and the retuned batch gives the same window up
-    to FP32 reassociation inside a team; a non-positive budget is rejected."""
+def _window_inputs(sim, h):
+    from paper_2204_07137_gb300 import inputs as I
+    q0 = sim.pack([I.initial_state(m, n, 0)[0] for m, n in sim.groups], "q")
+    qd0 = sim.pack([I.initial_state(m, n, 0)[1] for m, n in sim.groups], "qd")
+    act = torch.cat([torch.from_numpy(I.window_actions(m, n, h, 0).reshape(h, -1)) for m, n in sim.groups],
+                    dim=1).cuda().contiguous()
+    return q0, qd0, act
+
+
+@pytest.mark.parametrize("tape", [False, True])
+def test_native_autotune_keeps_a_valid_shape(tape):
+    """shac_autotune (the library's measured search) on a heterogeneous batch,
+    with and without the window tape: a valid shape is left applied, the
+    windows it times (in the caller's buffer of shac_autotune_workspace_bytes)
+    do not disturb the caller's inputs, and the retuned batch gives the same
+    window up to FP32 reassociation inside a team; a non-positive budget is
+    rejected."""
     import numpy as np
-    from paper_2204_07137_gb300 import _lib, autotune
+    from paper_2204_07137_gb300 import _lib
     from paper_2204_07137_gb300.sim import Simulator
     groups = [(_inputs().cartpole(), 40), (_inputs().ant(), 13)]
     tuned = Simulator(groups, form="batched", h_max=2)
-    tuned.set_window_tape(True)
     ref = Simulator(groups, form="batched", h_max=2)
-    ref.set_window_tape(True)
-    x = autotune._Inputs(ref, 2)
+    if tape:
+        tuned.set_window_tape(True)
+        ref.set_window_tape(True)
+    L = _lib.load()
+    assert L.shac_autotune_workspace_bytes(tuned.batch) > L.shac_batch_workspace_bytes(tuned.batch)
+    q0, qd0, act = _window_inputs(ref, 2)
+    keep = [t.clone() for t in (q0, qd0, act)]
     shapes = tuned.autotune_native(budget_ms=5000)
     assert len(shapes) == 2
-    assert all(l in autotune.LANES and w in autotune.WARPS for l, w in shapes)
-    a = tuned.window_forward(x.q0, x.qd0, x.act)
-    b = ref.window_forward(x.q0, x.qd0, x.act)
+    assert all(l in LANES and w in WARPS for l, w in shapes)
+    assert all(torch.equal(a, b) for a, b in zip(keep, (q0, qd0, act)))
+    a = tuned.window_forward(q0, qd0, act)
+    b = ref.window_forward(q0, qd0, act)
     torch.cuda.synchronize()
     for u, v in zip(a, b):
         np.testing.assert_allclose(u.cpu().numpy(), v.cpu().numpy(), rtol=1e-4, atol=1e-3)

@@ -136,6 +136,10 @@ def parse():
                    help="time learning episodes of the short-horizon actor-critic learner instead of the contract "
                         "line (the paper's per-episode forward / backward / critic split)")
     p.add_argument("--shac-envs", type=int, default=64)
+    p.add_argument("--policy", action="store_true",
+                   help="config 5 with the policy MLP in the loop (workload mtu-512): graph-captured window of "
+                        "policy + library steps + autograd through the step adjoints, timed beside the step loop "
+                        "without the network and the open-loop window")
     return p.parse_args()
 
 
@@ -510,7 +514,8 @@ def gpu_main(args, rank, world, dist):
                             "ms_per_window": ms_default},
                 "chosen": {"lanes_per_env": [l for l, _ in shape], "warps_per_cta": shape[0][1]},
                 "search": "coordinate descent over lanes per environment (each group) then warps per CTA, "
-                          f"h = 4 windows from the rest configuration, budget {args.autotune_ms} ms"}
+                          f"h = 8 windows from the rest configuration (median of 3; a change needs a 3 % gain), budget "
+                          f"{args.autotune_ms} ms"}
     shape = [sim.get_launch(g) for g in range(len(groups))]
 
     # ---- the configured variant: graph-captured forward + recomputing adjoint
@@ -576,12 +581,12 @@ def gpu_main(args, rank, world, dist):
     done_frac = float(oef[3].float().mean())
     del graph_ep
 
-    # gradient validity gate: sampled environments of every group against the FP64 oracle
+    # the outputs the CPU leg checks (sampled gradients of every group)
     graph.replay()
     torch.cuda.synchronize()
-    grad = None
-    if rank == 0 and args.grad_check_envs > 0:
-        grad = gradient_check(sim, groups, outf, outa, act, rbar, n_sample=args.grad_check_envs)
+    check_data = None
+    if rank == 0 and not args.no_cpu_baseline and args.grad_check_envs > 0:
+        check_data = [x.detach().clone() for x in tuple(outf) + tuple(outa)]
 
     # ---- plain form on the same inputs
     plain = make("plain")
@@ -689,7 +694,6 @@ def gpu_main(args, rank, world, dist):
                      "rule": "root below the task height or the task horizon; seeded reset states; "
                              "forward + adjoint with the gradient cut at resets, one CUDA graph"},
         "kernels_ms": {"k_batched_forward": ms_fwd, "k_batched_adjoint (recompute)": ms_adj},
-        "grad_rel_err": grad,
         "gpu_launches": 2 * args.steps,
         "clocks": clocks,
         "e2e": {"value": env_steps / (ms_e2e * 1e-3), "unit": "env-steps/s", "h2d_bytes_per_step": h2d,
@@ -713,12 +717,17 @@ def gpu_main(args, rank, world, dist):
                       "peak_source": hbm_src}},
     }
     if not args.no_cpu_baseline:
+        # CPU leg: the FP64 oracle timed on the host cores, and the gradient
+        # validity gate (sampled environments of every group against it)
         r, threads, dt, desc = oracle_workload_rate(groups, seed=0, target_s=12.0)
         line["cpu_baseline"] = {"value": r, "unit": "env-steps/s", "cores": threads, "kind": "oracle",
                                 "cpu_model": host_cpu_model(),
                                 "sample": f"{desc}, forward + exact adjoint, {dt:.1f} s; rate extrapolated to the "
                                           f"workload",
                                 "single_core": oracle_single_core_rate(args.workload)}
+        if check_data is not None:
+            cf, ca = check_data[:3], check_data[3:]
+            line["grad_rel_err"] = gradient_check(sim, groups, cf, ca, act, rbar, n_sample=args.grad_check_envs)
     print(json.dumps(line), flush=True)
 
 
@@ -764,6 +773,101 @@ def gradient_check(sim, groups, outf, outa, act, rbar, n_sample: int = 4):
         out[f"{gi}:{model.name}"] = {"max": float(rel.max()), "envs": envs.tolist(), "rel": rel.tolist()}
         off += N
     return out
+
+
+def policy_main(args, rank, world, dist):
+    """Config 5 with the policy in the loop: the window of h = 32 steps in which
+    every step's actions come from the MLP (obs -> 256 -> 128 -> muscles) and
+    the loss's gradient flows through the library's step adjoints into the
+    policy parameters (one CUDA graph: forward, loss, backward).  Timed beside
+    the same step loop with given actions (no network; gradient with respect
+    to the actions) and the open-loop window calls (two launches).  Each rank
+    its own shard (weak scaling); env-steps/s = N h / time."""
+    import torch
+    from paper_2204_07137_gb300 import build, inputs as I
+    from paper_2204_07137_gb300.policy import PolicyMLP, observation_size, policy_window_loss
+    from paper_2204_07137_gb300.sim import Simulator
+
+    build.build()
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    wl = I.workload(args.workload)
+    if len(wl.groups) != 1 or not wl.groups[0][0].n_muscles:
+        raise SystemExit("--policy needs a single muscle-actuated group (mtu-512)")
+    model, N = wl.groups[0]
+    seed = shard_seed(rank)
+    sim = Simulator(wl.groups, form="batched", h_max=1)
+    g = torch.Generator().manual_seed(seed)
+    pol = PolicyMLP(observation_size(model), model.na, generator=g).to(dev)
+    params = list(pol.parameters())
+    q0 = sim.pack([I.initial_state(model, N, seed)[0]], "q")
+    qd0 = sim.pack([I.initial_state(model, N, seed)[1]], "qd")
+    acts = torch.from_numpy(I.window_actions(model, N, H, seed).reshape(H, -1)).to(dev).contiguous()
+    acts.requires_grad_(True)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    timed = Timer(stream, flush, dist)
+
+    def capture(fn):
+        with torch.cuda.stream(stream):
+            for _ in range(2):
+                fn()
+        stream.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(stream):
+            with torch.cuda.graph(graph, stream=stream):
+                out = fn()
+        stream.synchronize()
+        return graph, out
+
+    def with_policy():
+        loss = policy_window_loss(sim, pol, q0, qd0, H)
+        return (loss,) + tuple(torch.autograd.grad(loss, params))
+
+    def without_policy():
+        loss = policy_window_loss(sim, pol, q0, qd0, H, actions=acts)
+        return loss, torch.autograd.grad(loss, [acts])[0]
+
+    g_pol, out_pol = capture(with_policy)
+    g_act, out_act = capture(without_policy)
+    wsim = Simulator(wl.groups, form="batched", h_max=H)
+    rbar = torch.full((H, N), 1.0 / (N * H), device=dev)
+    zq = torch.zeros(H + 1, wsim.q_size, device=dev)
+    zqd = torch.zeros(H + 1, wsim.qd_size, device=dev)
+    a_det = acts.detach()
+    g_win, _, outa = capture_window(wsim, q0, qd0, a_det, rbar, zq, zqd, stream)
+    sampler = ClockSampler(dev.index) if rank == 0 else None
+    if sampler:
+        sampler.start()
+    ms_pol = timed(g_pol.replay, args.steps, args.warmup)
+    clocks = sampler.stop() if sampler else None
+    ms_act = timed(g_act.replay, args.steps, args.warmup)
+    ms_win = timed(g_win.replay, args.steps, args.warmup)
+    torch.cuda.synchronize()
+    finite = all(bool(torch.isfinite(x).all()) for x in tuple(out_pol) + tuple(out_act) + tuple(outa))
+    ms_pol, ms_act, ms_win = max_over_ranks([ms_pol, ms_act, ms_win], dist, dev)
+    if rank != 0:
+        return
+    env_steps = N * H * world
+    n_params = sum(p.numel() for p in params)
+    line = {
+        "metric": METRIC + " (policy in the loop)", "value": env_steps / (ms_pol * 1e-3), "unit": "env-steps/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_pol,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": wl.name + " policy-in-the-loop", "n_envs_per_gpu": N, "h": H,
+                   "substeps": model.substeps, "policy": f"MLP {observation_size(model)}-256-128-{model.na}, ELU, "
+                                                       f"sigmoid; {n_params} parameters, weights ~ N(0, 0.05)",
+                   "form": "per step: observation, MLP, library step (shac_step); backward: autograd through "
+                           "the library's step adjoint (substeps recomputed) into the MLP; one CUDA graph",
+                   "timing": "median of the timed steps", "l2": "flushed (256 MB write) before each timed step"},
+        "without_policy": {"value": env_steps / (ms_act * 1e-3), "unit": "env-steps/s", "ms_per_step": ms_act,
+                           "form": "the same step loop with given actions, gradient w.r.t. the actions"},
+        "open_loop_window": {"value": env_steps / (ms_win * 1e-3), "unit": "env-steps/s", "ms_per_step": ms_win,
+                             "form": "shac_window_forward + shac_window_adjoint, one CUDA graph"},
+        "finite": finite, "clocks": clocks,
+        "gpu_launches": 2 * H * args.steps,
+    }
+    print(json.dumps(line), flush=True)
 
 
 def profile_case_main(args):
@@ -816,6 +920,8 @@ def main():
         elif args.profile_case:
             if rank == 0:
                 profile_case_main(args)
+        elif args.policy:
+            policy_main(args, rank, world, dist)
         elif args.h_sweep:
             if rank == 0:
                 h_sweep_main(args)

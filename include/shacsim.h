@@ -292,11 +292,12 @@ shac_status shac_batch_get_launch(const shac_batch* batch, int32_t group, int32_
  * kernels are one thread per environment).  Coordinate descent: each group's
  * lanes per environment in turn (1, 2, 4, 8, 16, 32; the others fixed), then
  * the warps per CTA (1, 2, 4, 8); every candidate is timed as a window forward
- * + window adjoint of min(h_max, 4) steps with CUDA events on `stream` (one
- * warm-up, best of two), from the rest configuration (joint coordinates 0,
+ * + window adjoint of min(h_max, 8) steps with CUDA events on `stream` (one
+ * warm-up, median of three), from the rest configuration (joint coordinates 0,
  * free joints at the origin with the identity orientation, zero velocities and
- * actions).  The fastest shape is applied to the batch (as
- * shac_batch_set_launch would) and kept.  `workspace`: a caller buffer of
+ * actions).  A candidate replaces the best shape so far only when it is more
+ * than 3 % faster (timing noise between equal shapes stays below that); the
+ * best shape is applied to the batch (as shac_batch_set_launch would) and kept.  `workspace`: a caller buffer of
  * shac_autotune_workspace_bytes (256-byte aligned), overwritten: the batch's
  * workspace followed by the inputs and outputs of the timed windows; the call
  * allocates no device memory.  budget_ms: wall-clock limit of the search

@@ -81,12 +81,31 @@ def lib():
         L.orc_muscle_lengths.argtypes = [D, _f64p, _f64p]
         L.orc_cholesky.argtypes = [i32, _f64p, _f64p]
         L.orc_num_threads.restype = ctypes.c_int
+        u64, f64 = ctypes.c_uint64, ctypes.c_double
+        L.orc_mca_step.argtypes = [D, i32, _f64p, _f64p, _f64p, _f64p, _f64p, _f64p, u64, f64]
+        L.orc_mca_window_adjoint.argtypes = [D, i32, i32, _f64p, _f64p, _f64p, _f64p, _f64p, _f64p,
+                                             _f64p, _f64p, _f64p, u64, f64, i32]
+        L.orc_mca_chol_solve.argtypes = [i32, _f64p, _f64p, _f64p, u64, f64]
         _lib = L
     return _lib
 
 
 def num_threads() -> int:
     return int(lib().orc_num_threads())
+
+
+# Unit roundoff of FP32 (round to nearest): the relative size of the Monte
+# Carlo Arithmetic perturbations that stand for FP32 rounding.
+U_FP32 = 2.0 ** -24
+
+
+def mca_chol_solve(A, b, seed: int, u: float = U_FP32):
+    """x = A^{-1} b by Cholesky in Monte Carlo Arithmetic (see shac_oracle.cpp)."""
+    A, pA = _d(A)
+    b, pb = _d(b)
+    x = np.zeros(b.shape[0])
+    lib().orc_mca_chol_solve(int(b.shape[0]), pA, pb, x.ctypes.data_as(_f64p), int(seed), float(u))
+    return x
 
 
 def _d(a):
@@ -304,6 +323,41 @@ class Oracle:
         q, pq = _d(q)
         lib().orc_muscle_lengths(ctypes.byref(self.desc), pq, out.ctypes.data_as(_f64p))
         return out[: self.model.n_muscles]
+
+    # ---- FP32 error floor (Monte Carlo Arithmetic; see shac_oracle.cpp) ----
+    def mca_step(self, q, qd, a, seed: int, u: float = U_FP32):
+        """step() with every operation perturbed at relative size u (seeded
+        per environment); u = 0 gives step() exactly."""
+        q, pq = _d(q); qd, pqd = _d(qd); a, pa = _d(a)
+        N = q.shape[0]
+        qn = np.zeros((N, self.nq)); qdn = np.zeros((N, self.nv)); r = np.zeros(N)
+        lib().orc_mca_step(ctypes.byref(self.desc), N, pq, pqd, pa, qn.ctypes.data_as(_f64p),
+                           qdn.ctypes.data_as(_f64p), r.ctypes.data_as(_f64p), int(seed), float(u))
+        return qn, qdn, r
+
+    def mca_window_adjoint(self, q_traj, qd_traj, act, r_bar, qT_bar, qdT_bar, seed: int, u: float = U_FP32,
+                           tangents: bool = True):
+        """window_adjoint() with each step's Jacobian taken along a perturbed
+        evaluation of the step (values perturbed at relative size u; with
+        tangents, every operation of the derivative computation as well)."""
+        arrs = [_d(x) for x in (q_traj, qd_traj, act, r_bar, qT_bar, qdT_bar)]
+        h, N = arrs[2][0].shape[0], arrs[2][0].shape[1]
+        qb = np.zeros((N, self.nq)); qdb = np.zeros((N, self.nv)); ab = np.zeros((h, N, self.na))
+        lib().orc_mca_window_adjoint(ctypes.byref(self.desc), N, h, *[p for _, p in arrs],
+                                     qb.ctypes.data_as(_f64p), qdb.ctypes.data_as(_f64p), ab.ctypes.data_as(_f64p),
+                                     int(seed), float(u), int(bool(tangents)))
+        return qb, qdb, ab
+
+    def step_floor(self, q, qd, a, runs: int = 3, seed: int = 0):
+        """Per-component FP32 floor of one step: the largest deviation from the
+        exact result over `runs` Monte Carlo Arithmetic runs.
+        -> (exact (qn, qdn, r), floor (fq, fqd, fr))."""
+        ex = self.step(q, qd, a)
+        fl = [np.zeros_like(x) for x in ex]
+        for k in range(runs):
+            for f, y, x in zip(fl, self.mca_step(q, qd, a, seed=seed * 1000 + k), ex):
+                np.maximum(f, np.abs(y - x), out=f)
+        return ex, tuple(fl)
 
 
 def cholesky(A):

@@ -25,9 +25,19 @@
 //     exactly by forward-mode dual numbers (no hand-written reverse code);
 //   * the window adjoint as the concatenation of step adjoints (appendix A.1).
 //
-// All functions are templated on the scalar T (double or Dual<ND>).
+// All functions are templated on the scalar T (double or a dual number).
 // Branches (contact, friction regime, joint limits, clipping) are decided on
 // the value part.
+//
+// FP32 error floor (a diagnostic, never a reference value): the same functions
+// instantiated on Monte Carlo Arithmetic scalars (Parker, "Monte Carlo
+// Arithmetic", 1997), whose every operation result is multiplied by a random
+// factor 1 + u r, r uniform in [-1, 1), u = 2^-24 (the unit roundoff of
+// FP32).  Over a few seeded runs, the spread of an output measures how far
+// rounding every intermediate result to FP32 moves it: the floor below which
+// an FP32 implementation of the map cannot be expected to agree with the
+// exact FP64 result.  With u = 0 the perturbed runs equal the FP64 oracle bit
+// for bit.
 
 #include <cmath>
 #include <cstdint>
@@ -44,34 +54,96 @@ namespace orc {
 // ---------------------------------------------------------------- scalars --
 constexpr int ND = 16;   // tangent directions carried per dual pass
 
-struct Dual {
+// Monte Carlo Arithmetic state of the calling thread: a splitmix64 generator
+// (Steele, Lea and Flood, "Fast splittable pseudorandom number generators",
+// 2014) and the relative perturbation size u (0: exact FP64).
+struct McaState { uint64_t s = 0; double u = 0.0; };
+static thread_local McaState g_mca;
+
+inline uint64_t splitmix64_next(uint64_t& x) {
+  x += 0x9E3779B97F4A7C15ull;
+  uint64_t z = x;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+inline void mca_seed(uint64_t seed, uint64_t stream, double u) {
+  g_mca.s = seed * 0xD1B54A32D192ED03ull + stream;
+  splitmix64_next(g_mca.s);
+  g_mca.u = u;
+}
+// x (1 + u r), r uniform in [-1, 1) from the top 53 bits of the generator
+inline double mca_round(double x) {
+  if (g_mca.u == 0.0) return x;
+  const double r = (double)(splitmix64_next(g_mca.s) >> 11) * 0x1.0p-53 * 2.0 - 1.0;
+  return x * (1.0 + g_mca.u * r);
+}
+
+// Rounding policies of the dual numbers: exact (the oracle), the value part
+// perturbed after every operation (tangents exact), or values and tangents
+// perturbed (every operation of the derivative computation as well).
+struct Exact { static double fix(double x) { return x; } static double fixd(double x) { return x; } };
+struct McaValue { static double fix(double x) { return mca_round(x); } static double fixd(double x) { return x; } };
+struct McaFull { static double fix(double x) { return mca_round(x); } static double fixd(double x) { return mca_round(x); } };
+
+template <class P>
+struct DualT {
   double v;
   double d[ND];
-  Dual() : v(0.0) { for (int i = 0; i < ND; ++i) d[i] = 0.0; }
-  Dual(double x) : v(x) { for (int i = 0; i < ND; ++i) d[i] = 0.0; }
+  DualT() : v(0.0) { for (int i = 0; i < ND; ++i) d[i] = 0.0; }
+  DualT(double x) : v(x) { for (int i = 0; i < ND; ++i) d[i] = 0.0; }
 };
-inline Dual operator+(const Dual& a, const Dual& b) { Dual r; r.v = a.v + b.v; for (int i = 0; i < ND; ++i) r.d[i] = a.d[i] + b.d[i]; return r; }
-inline Dual operator-(const Dual& a, const Dual& b) { Dual r; r.v = a.v - b.v; for (int i = 0; i < ND; ++i) r.d[i] = a.d[i] - b.d[i]; return r; }
-inline Dual operator-(const Dual& a) { Dual r; r.v = -a.v; for (int i = 0; i < ND; ++i) r.d[i] = -a.d[i]; return r; }
-inline Dual operator*(const Dual& a, const Dual& b) { Dual r; r.v = a.v * b.v; for (int i = 0; i < ND; ++i) r.d[i] = a.d[i] * b.v + a.v * b.d[i]; return r; }
-inline Dual operator/(const Dual& a, const Dual& b) {
-  Dual r; r.v = a.v / b.v; double ib = 1.0 / (b.v * b.v);
-  for (int i = 0; i < ND; ++i) r.d[i] = (a.d[i] * b.v - a.v * b.d[i]) * ib; return r;
+template <class P> inline DualT<P> operator+(const DualT<P>& a, const DualT<P>& b) { DualT<P> r; r.v = P::fix(a.v + b.v); for (int i = 0; i < ND; ++i) r.d[i] = P::fixd(a.d[i] + b.d[i]); return r; }
+template <class P> inline DualT<P> operator-(const DualT<P>& a, const DualT<P>& b) { DualT<P> r; r.v = P::fix(a.v - b.v); for (int i = 0; i < ND; ++i) r.d[i] = P::fixd(a.d[i] - b.d[i]); return r; }
+template <class P> inline DualT<P> operator-(const DualT<P>& a) { DualT<P> r; r.v = -a.v; for (int i = 0; i < ND; ++i) r.d[i] = -a.d[i]; return r; }
+template <class P> inline DualT<P> operator*(const DualT<P>& a, const DualT<P>& b) { DualT<P> r; r.v = P::fix(a.v * b.v); for (int i = 0; i < ND; ++i) r.d[i] = P::fixd(P::fixd(a.d[i] * b.v) + P::fixd(a.v * b.d[i])); return r; }
+template <class P> inline DualT<P> operator/(const DualT<P>& a, const DualT<P>& b) {
+  DualT<P> r; r.v = P::fix(a.v / b.v); double ib = P::fixd(1.0 / P::fixd(b.v * b.v));
+  for (int i = 0; i < ND; ++i) r.d[i] = P::fixd(P::fixd(P::fixd(a.d[i] * b.v) - P::fixd(a.v * b.d[i])) * ib); return r;
 }
-inline Dual operator+(const Dual& a, double b) { Dual r = a; r.v += b; return r; }
-inline Dual operator+(double a, const Dual& b) { Dual r = b; r.v += a; return r; }
-inline Dual operator-(const Dual& a, double b) { Dual r = a; r.v -= b; return r; }
-inline Dual operator-(double a, const Dual& b) { Dual r = -b; r.v += a; return r; }
-inline Dual operator*(const Dual& a, double b) { Dual r; r.v = a.v * b; for (int i = 0; i < ND; ++i) r.d[i] = a.d[i] * b; return r; }
-inline Dual operator*(double a, const Dual& b) { return b * a; }
-inline Dual operator/(const Dual& a, double b) { return a * (1.0 / b); }
-inline Dual& operator+=(Dual& a, const Dual& b) { a = a + b; return a; }
-inline Dual& operator-=(Dual& a, const Dual& b) { a = a - b; return a; }
-inline Dual& operator*=(Dual& a, const Dual& b) { a = a * b; return a; }
-inline Dual sqrt(const Dual& a) { Dual r; r.v = std::sqrt(a.v); double k = 0.5 / r.v; for (int i = 0; i < ND; ++i) r.d[i] = a.d[i] * k; return r; }
-inline Dual sin(const Dual& a) { Dual r; r.v = std::sin(a.v); double k = std::cos(a.v); for (int i = 0; i < ND; ++i) r.d[i] = a.d[i] * k; return r; }
-inline Dual cos(const Dual& a) { Dual r; r.v = std::cos(a.v); double k = -std::sin(a.v); for (int i = 0; i < ND; ++i) r.d[i] = a.d[i] * k; return r; }
-inline double val(const Dual& a) { return a.v; }
+template <class P> inline DualT<P> operator+(const DualT<P>& a, double b) { DualT<P> r = a; r.v = P::fix(r.v + b); return r; }
+template <class P> inline DualT<P> operator+(double a, const DualT<P>& b) { DualT<P> r = b; r.v = P::fix(r.v + a); return r; }
+template <class P> inline DualT<P> operator-(const DualT<P>& a, double b) { DualT<P> r = a; r.v = P::fix(r.v - b); return r; }
+template <class P> inline DualT<P> operator-(double a, const DualT<P>& b) { DualT<P> r = -b; r.v = P::fix(r.v + a); return r; }
+template <class P> inline DualT<P> operator*(const DualT<P>& a, double b) { DualT<P> r; r.v = P::fix(a.v * b); for (int i = 0; i < ND; ++i) r.d[i] = P::fixd(a.d[i] * b); return r; }
+template <class P> inline DualT<P> operator*(double a, const DualT<P>& b) { return b * a; }
+template <class P> inline DualT<P> operator/(const DualT<P>& a, double b) { return a * (1.0 / b); }
+template <class P> inline DualT<P>& operator+=(DualT<P>& a, const DualT<P>& b) { a = a + b; return a; }
+template <class P> inline DualT<P>& operator-=(DualT<P>& a, const DualT<P>& b) { a = a - b; return a; }
+template <class P> inline DualT<P>& operator*=(DualT<P>& a, const DualT<P>& b) { a = a * b; return a; }
+template <class P> inline DualT<P> sqrt(const DualT<P>& a) { DualT<P> r; r.v = P::fix(std::sqrt(a.v)); double k = P::fixd(0.5 / r.v); for (int i = 0; i < ND; ++i) r.d[i] = P::fixd(a.d[i] * k); return r; }
+template <class P> inline DualT<P> sin(const DualT<P>& a) { DualT<P> r; r.v = P::fix(std::sin(a.v)); double k = P::fixd(std::cos(a.v)); for (int i = 0; i < ND; ++i) r.d[i] = P::fixd(a.d[i] * k); return r; }
+template <class P> inline DualT<P> cos(const DualT<P>& a) { DualT<P> r; r.v = P::fix(std::cos(a.v)); double k = P::fixd(-std::sin(a.v)); for (int i = 0; i < ND; ++i) r.d[i] = P::fixd(a.d[i] * k); return r; }
+template <class P> inline double val(const DualT<P>& a) { return a.v; }
+using Dual = DualT<Exact>;
+
+// Monte Carlo Arithmetic scalar: a double whose every operation result is
+// perturbed (mca_round).
+struct Mca {
+  double v;
+  Mca() : v(0.0) {}
+  Mca(double x) : v(x) {}
+};
+inline Mca operator+(const Mca& a, const Mca& b) { return Mca(mca_round(a.v + b.v)); }
+inline Mca operator-(const Mca& a, const Mca& b) { return Mca(mca_round(a.v - b.v)); }
+inline Mca operator-(const Mca& a) { return Mca(-a.v); }
+inline Mca operator*(const Mca& a, const Mca& b) { return Mca(mca_round(a.v * b.v)); }
+inline Mca operator/(const Mca& a, const Mca& b) { return Mca(mca_round(a.v / b.v)); }
+inline Mca operator+(const Mca& a, double b) { return Mca(mca_round(a.v + b)); }
+inline Mca operator+(double a, const Mca& b) { return Mca(mca_round(a + b.v)); }
+inline Mca operator-(const Mca& a, double b) { return Mca(mca_round(a.v - b)); }
+inline Mca operator-(double a, const Mca& b) { return Mca(mca_round(a - b.v)); }
+inline Mca operator*(const Mca& a, double b) { return Mca(mca_round(a.v * b)); }
+inline Mca operator*(double a, const Mca& b) { return Mca(mca_round(a * b.v)); }
+inline Mca operator/(const Mca& a, double b) { return Mca(mca_round(a.v / b)); }
+inline Mca& operator+=(Mca& a, const Mca& b) { a = a + b; return a; }
+inline Mca& operator-=(Mca& a, const Mca& b) { a = a - b; return a; }
+inline Mca& operator*=(Mca& a, const Mca& b) { a = a * b; return a; }
+inline Mca sqrt(const Mca& a) { return Mca(mca_round(std::sqrt(a.v))); }
+inline Mca sin(const Mca& a) { return Mca(mca_round(std::sin(a.v))); }
+inline Mca cos(const Mca& a) { return Mca(mca_round(std::cos(a.v))); }
+inline double val(const Mca& a) { return a.v; }
+
 inline double val(double a) { return a; }
 using std::sqrt; using std::sin; using std::cos;
 
@@ -532,32 +604,35 @@ void step(const Model& m, const T* q, const T* qd, const T* act, T* qn, T* qdn, 
 }
 
 // Exact step Jacobian: rows (q_next[nq], qd_next[nv], reward[1]),
-// columns (q[nq], qd[nv], act[na]); row-major, by dual-number passes.
+// columns (q[nq], qd[nv], act[na]); row-major, by dual-number passes (D = Dual;
+// DualT<McaValue> gives the derivatives along an FP32-perturbed evaluation).
+template <class D = Dual>
 void step_jacobian(const Model& m, const double* q, const double* qd, const double* act, double* J) {
   const int nin = m.nq + m.nv + m.na, nout = m.nq + m.nv + 1;
-  std::vector<Dual> x(nin), qn(m.nq), qdn(m.nv);
-  Dual r;
+  std::vector<D> x(nin), qn(m.nq), qdn(m.nv);
+  D r;
   for (int base = 0; base < nin; base += ND) {
     for (int i = 0; i < nin; ++i) {
       double v = i < m.nq ? q[i] : (i < m.nq + m.nv ? qd[i - m.nq] : act[i - m.nq - m.nv]);
-      x[i] = Dual(v);
+      x[i] = D(v);
       if (i >= base && i < base + ND) x[i].d[i - base] = 1.0;
     }
     step(m, x.data(), x.data() + m.nq, x.data() + m.nq + m.nv, qn.data(), qdn.data(), &r);
     for (int o = 0; o < nout; ++o) {
-      const Dual& y = o < m.nq ? qn[o] : (o < m.nq + m.nv ? qdn[o - m.nq] : r);
+      const D& y = o < m.nq ? qn[o] : (o < m.nq + m.nv ? qdn[o - m.nq] : r);
       for (int i = base; i < std::min(nin, base + ND); ++i) J[o * nin + i] = y.d[i - base];
     }
   }
 }
 
 // Eq. backward: (dL/ds_t, dL/da_t) = (dL/ds_{t+1}, dL/dr_t) [dF/ds_t, dF/da_t].
+template <class D = Dual>
 void step_vjp(const Model& m, const double* q, const double* qd, const double* act,
               const double* qn_bar, const double* qdn_bar, double r_bar,
               double* q_bar, double* qd_bar, double* act_bar) {
   const int nin = m.nq + m.nv + m.na, nout = m.nq + m.nv + 1;
   std::vector<double> J((size_t)nout * nin), ybar(nout);
-  step_jacobian(m, q, qd, act, J.data());
+  step_jacobian<D>(m, q, qd, act, J.data());
   for (int o = 0; o < m.nq; ++o) ybar[o] = qn_bar[o];
   for (int o = 0; o < m.nv; ++o) ybar[m.nq + o] = qdn_bar[o];
   ybar[nout - 1] = r_bar;
@@ -722,6 +797,74 @@ void orc_window_adjoint(const orc_desc* d, int32_t N, int32_t h, const double* q
     for (int j = 0; j < m.nq; ++j) q0_bar[(size_t)e * m.nq + j] = qb[j];
     for (int j = 0; j < m.nv; ++j) qd0_bar[(size_t)e * m.nv + j] = qdb[j];
   }
+}
+
+// ---- FP32 error floor: Monte Carlo Arithmetic runs -------------------------
+// Each environment e draws its perturbations from its own stream (seed, e), so
+// results do not depend on the thread that runs it.  u = 0 gives the exact
+// FP64 results.
+
+void orc_mca_step(const orc_desc* d, int32_t N, const double* q, const double* qd, const double* act,
+                  double* qn, double* qdn, double* r, uint64_t seed, double u) {
+  orc::Model m = make_model(d);
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int e = 0; e < N; ++e) {
+    orc::mca_seed(seed, (uint64_t)e, u);
+    std::vector<orc::Mca> x(m.nq + m.nv + m.na), yq(m.nq), yqd(m.nv);
+    for (int j = 0; j < m.nq; ++j) x[j] = orc::Mca(q[(size_t)e * m.nq + j]);
+    for (int j = 0; j < m.nv; ++j) x[m.nq + j] = orc::Mca(qd[(size_t)e * m.nv + j]);
+    for (int j = 0; j < m.na; ++j) x[m.nq + m.nv + j] = orc::Mca(act[(size_t)e * m.na + j]);
+    orc::Mca rr;
+    orc::step<orc::Mca>(m, x.data(), x.data() + m.nq, x.data() + m.nq + m.nv, yq.data(), yqd.data(), &rr);
+    for (int j = 0; j < m.nq; ++j) qn[(size_t)e * m.nq + j] = yq[j].v;
+    for (int j = 0; j < m.nv; ++j) qdn[(size_t)e * m.nv + j] = yqd[j].v;
+    r[e] = rr.v;
+    orc::mca_seed(0, 0, 0.0);
+  }
+}
+
+// The window adjoint (as orc_window_adjoint) with every step's Jacobian taken
+// along an FP32-perturbed evaluation of the step; tangents != 0 perturbs the
+// derivative arithmetic too.
+void orc_mca_window_adjoint(const orc_desc* d, int32_t N, int32_t h, const double* q_traj, const double* qd_traj,
+                            const double* act, const double* r_bar, const double* qT_bar, const double* qdT_bar,
+                            double* q0_bar, double* qd0_bar, double* act_bar, uint64_t seed, double u,
+                            int32_t tangents) {
+  orc::Model m = make_model(d);
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int e = 0; e < N; ++e) {
+    orc::mca_seed(seed, (uint64_t)e, u);
+    std::vector<double> qb(qT_bar + (size_t)e * m.nq, qT_bar + (size_t)(e + 1) * m.nq);
+    std::vector<double> qdb(qdT_bar + (size_t)e * m.nv, qdT_bar + (size_t)(e + 1) * m.nv);
+    std::vector<double> qb2(m.nq), qdb2(m.nv);
+    for (int t = h - 1; t >= 0; --t) {
+      const double* qt = q_traj + ((size_t)t * N + e) * m.nq;
+      const double* qdt = qd_traj + ((size_t)t * N + e) * m.nv;
+      const double* at = act + ((size_t)t * N + e) * m.na;
+      double* abt = act_bar + ((size_t)t * N + e) * m.na;
+      if (tangents)
+        orc::step_vjp<orc::DualT<orc::McaFull>>(m, qt, qdt, at, qb.data(), qdb.data(), r_bar[(size_t)t * N + e],
+                                                 qb2.data(), qdb2.data(), abt);
+      else
+        orc::step_vjp<orc::DualT<orc::McaValue>>(m, qt, qdt, at, qb.data(), qdb.data(), r_bar[(size_t)t * N + e],
+                                                  qb2.data(), qdb2.data(), abt);
+      qb.swap(qb2); qdb.swap(qdb2);
+    }
+    for (int j = 0; j < m.nq; ++j) q0_bar[(size_t)e * m.nq + j] = qb[j];
+    for (int j = 0; j < m.nv; ++j) qd0_bar[(size_t)e * m.nv + j] = qdb[j];
+    orc::mca_seed(0, 0, 0.0);
+  }
+}
+
+// Cholesky factorisation and solve of one n x n system in Monte Carlo
+// Arithmetic (the pins check the floor's scaling with the condition number).
+void orc_mca_chol_solve(int32_t n, const double* A, const double* b, double* x, uint64_t seed, double u) {
+  orc::mca_seed(seed, 0, u);
+  std::vector<orc::Mca> Am(A, A + (size_t)n * n), Lc((size_t)n * n), bm(b, b + n), xm(n);
+  orc::cholesky<orc::Mca>(n, Am.data(), Lc.data());
+  orc::chol_solve<orc::Mca>(n, Lc.data(), bm.data(), xm.data());
+  for (int i = 0; i < n; ++i) x[i] = xm[i].v;
+  orc::mca_seed(0, 0, 0.0);
 }
 
 // ---- single-state helpers used by the pins --------------------------------

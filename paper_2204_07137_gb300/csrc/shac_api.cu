@@ -838,9 +838,12 @@ extern "C" const char* shac_status_string(shac_status s) {
 }
 
 // -------------------------------------------------------------- autotune --
-// Inputs and outputs of the autotuner's timed windows (h = min(h_max, 4)
+// Inputs and outputs of the autotuner's timed windows (h = min(h_max, 8)
 // steps), carved from the caller's workspace after the batch's own part.
-static const int AUTOTUNE_MAX_H = 4;
+static const int AUTOTUNE_MAX_H = 8;
+// A candidate shape replaces the best one only when its window is faster by
+// more than this fraction (timing noise between equal shapes is ~1-3 %).
+static const float AUTOTUNE_MARGIN = 0.03f;
 
 static size_t autotune_parts(const shac_batch* b, size_t* parts) {
   const size_t h = (size_t)std::min(b->h_max, AUTOTUNE_MAX_H);
@@ -903,22 +906,25 @@ extern "C" shac_status shac_autotune(shac_batch* b, void* stream, void* ws, int3
     return run_adjoint(b, s, ws, h, qt, qdt, act, rbar, qtb, qdtb, qtb + (size_t)h * nq, qdtb + (size_t)h * nqd,
                        q0b, qd0b, actb, nullptr, true);
   };
-  // ms per window of the current shape (infinite if the shape does not launch)
+  // ms per window of the current shape: median of three after one warm-up
+  // (infinite if the shape does not launch)
   auto measure = [&](float* ms) -> shac_status {
     *ms = INFINITY;
     shac_status r = window();
     if (r == SHAC_ERR_CAPACITY) return SHAC_OK;
     if (r != SHAC_OK) return r;
-    for (int rep = 0; rep < 2; ++rep) {
+    float t[3];
+    for (int rep = 0; rep < 3; ++rep) {
       if (cudaEventRecord(e0, s) != cudaSuccess) return SHAC_ERR_CUDA;
       if ((r = window()) != SHAC_OK) return r;
       if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) return SHAC_ERR_CUDA;
-      float t = 0.f;
-      if (cudaEventElapsedTime(&t, e0, e1) != cudaSuccess) return SHAC_ERR_CUDA;
-      *ms = std::min(*ms, t);
+      if (cudaEventElapsedTime(&t[rep], e0, e1) != cudaSuccess) return SHAC_ERR_CUDA;
     }
+    std::sort(t, t + 3);
+    *ms = t[1];
     return SHAC_OK;
   };
+  auto better = [](float t, float best) { return t < best * (1.f - AUTOTUNE_MARGIN); };
   const int n_groups = (int)b->groups.size();
   std::vector<int> lanes0(n_groups), best_lanes(n_groups);
   for (int gi = 0; gi < n_groups; ++gi) lanes0[gi] = best_lanes[gi] = b->groups[gi].lanes;
@@ -938,7 +944,7 @@ extern "C" shac_status shac_autotune(shac_batch* b, void* stream, void* ws, int3
       b->warps_per_cta = best_warps;
       if ((st = build_items(b)) != SHAC_OK) break;
       float t;
-      if ((st = measure(&t)) == SHAC_OK && t < best) { best = t; best_lanes[gi] = l; }
+      if ((st = measure(&t)) == SHAC_OK && better(t, best)) { best = t; best_lanes[gi] = l; }
     }
   }
   for (int w : kWarps) {
@@ -948,7 +954,7 @@ extern "C" shac_status shac_autotune(shac_batch* b, void* stream, void* ws, int3
     b->warps_per_cta = w;
     if ((st = build_items(b)) != SHAC_OK) break;
     float t;
-    if ((st = measure(&t)) == SHAC_OK && t < best) { best = t; best_warps = w; }
+    if ((st = measure(&t)) == SHAC_OK && better(t, best)) { best = t; best_warps = w; }
   }
   // keep the best shape (the starting one after an error)
   const bool ok = st == SHAC_OK;

@@ -74,22 +74,29 @@ class PolicyMLP(nn.Module):
 
 
 def policy_window_loss(sim: Simulator, policy: nn.Module, q0: torch.Tensor, qd0: torch.Tensor, h: int,
-                       keep: List | None = None) -> torch.Tensor:
+                       keep: List | None = None, env_weight: torch.Tensor | None = None,
+                       actions: torch.Tensor | None = None) -> torch.Tensor:
     """Negative mean reward of an h-step window with the policy in the loop
     (single-group simulator).  If ``keep`` is a list, the per-step states and
-    actions are appended to it (for checks)."""
+    actions are appended to it (for checks).  env_weight [N]: per-environment
+    weights of the rewards (default all ones).  actions [h, n_act * N]: given
+    open-loop actions instead of the policy's (the same step loop without the
+    network)."""
     assert len(sim.groups) == 1
     model, N = sim.groups[0]
     q, qd = q0, qd0
     total = q0.new_zeros(())
-    for _ in range(h):
-        obs = free_root_observation(q.view(model.nq, N), qd.view(model.nv, N))
-        a = policy(obs)                                   # [N, n_act]
-        a_soa = a.transpose(0, 1).contiguous().view(-1)   # [n_act * N]
+    for t in range(h):
+        if actions is None:
+            obs = free_root_observation(q.view(model.nq, N), qd.view(model.nv, N))
+            a = policy(obs)                                   # [N, n_act]
+            a_soa = a.transpose(0, 1).contiguous().view(-1)   # [n_act * N]
+        else:
+            a_soa = actions[t]
         if keep is not None:
             keep.append((q, qd, a_soa))
         q, qd, r = SimStep.apply(sim, q, qd, a_soa)
-        total = total + r.sum()
+        total = total + (r.sum() if env_weight is None else (env_weight * r).sum())
     if keep is not None:
         keep.append((q, qd, None))
     return -total / (N * h)

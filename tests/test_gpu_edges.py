@@ -5,7 +5,8 @@ inside a batch, which must change nothing for the others."""
 import numpy as np
 import pytest
 
-from helpers import assert_grad_close, assert_state_close, long_chain, model_by_name, seeded_case
+from helpers import (assert_grad_close, assert_state_close, long_chain, model_by_name, oracle_step_with_floor,
+                     seeded_case)
 from paper_2204_07137_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
@@ -39,10 +40,10 @@ def test_single_environment_step_and_adjoint(oracle_mod, form, name):
     q, qd, a = seeded_case(m, 1, 4, "initial")
     qn, qdn, r = sim.step(T(q), T(qd), T(a))
     torch.cuda.synchronize()
-    rq, rqd, rr = o.step(q.T, qd.T, a.T)
-    assert_state_close(qn.cpu().numpy().reshape(m.nq, 1).T, rq, f"{name}/{form} q_next")
-    assert_state_close(qdn.cpu().numpy().reshape(m.nv, 1).T, rqd, f"{name}/{form} qd_next")
-    assert_state_close(r.cpu().numpy(), rr, f"{name}/{form} reward")
+    (rq, rqd, rr), (fq, fqd, fr) = oracle_step_with_floor(o, q.T, qd.T, a.T)
+    assert_state_close(qn.cpu().numpy().reshape(m.nq, 1).T, rq, f"one env {name}/{form} q", fq)
+    assert_state_close(qdn.cpu().numpy().reshape(m.nv, 1).T, rqd, f"one env {name}/{form} qd", fqd)
+    assert_state_close(r.cpu().numpy(), rr, f"one env {name}/{form} reward", fr)
     rng = np.random.default_rng(8)
     qb = rng.normal(size=(m.nq, 1)).astype(np.float32)
     qdb = rng.normal(size=(m.nv, 1)).astype(np.float32)
@@ -94,9 +95,9 @@ def test_largest_model_step_and_adjoint(oracle_mod, form):
     a = I.window_actions(m, N, 1, 2)[0]
     qn, qdn, r = sim.step(T(q), T(qd), T(a))
     torch.cuda.synchronize()
-    rq, rqd, rr = o.step(q.T, qd.T, a.T)
-    assert_state_close(qn.cpu().numpy().reshape(m.nq, N).T, rq, f"chain32/{form} q_next")
-    assert_state_close(qdn.cpu().numpy().reshape(m.nv, N).T, rqd, f"chain32/{form} qd_next")
+    (rq, rqd, rr), (fq, fqd, fr) = oracle_step_with_floor(o, q.T, qd.T, a.T)
+    assert_state_close(qn.cpu().numpy().reshape(m.nq, N).T, rq, f"chain32/{form} q", fq)
+    assert_state_close(qdn.cpu().numpy().reshape(m.nv, N).T, rqd, f"chain32/{form} qd", fqd)
     rng = np.random.default_rng(3)
     qb = rng.normal(size=(m.nq, N)).astype(np.float32)
     qdb = rng.normal(size=(m.nv, N)).astype(np.float32)

@@ -8,7 +8,7 @@ for the expected state."""
 import numpy as np
 import pytest
 
-from helpers import airborne, assert_grad_close, assert_state_close
+from helpers import airborne, assert_grad_close, assert_state_close, oracle_step_with_floor
 from paper_2204_07137_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
@@ -80,8 +80,8 @@ def test_episodic_window_matches_oracle_step_by_step(oracle_mod, name, N):
     hq = _height_index(m) if thr > -np.inf else -1
     fired = 0
     for t in range(h):
-        pq, pqd, pr = o.step(gq[t], gqd[t], a[t])
-        assert_state_close(grw[t], pr, f"{name} reward step {t}")
+        (pq, pqd, pr), (fq, fqd, fr) = oracle_step_with_floor(o, gq[t], gqd[t], a[t])
+        assert_state_close(grw[t], pr, f"episodic {name} reward step {t}", fr)
         e = e + 1
         by_len = e >= H
         by_height = (pq[:, hq] < thr) if hq >= 0 else np.zeros(N, bool)
@@ -92,8 +92,8 @@ def test_episodic_window_matches_oracle_step_by_step(oracle_mod, name, N):
         np.testing.assert_array_equal(gq[t + 1][d], qr.T[d])      # reset states copied bit for bit
         np.testing.assert_array_equal(gqd[t + 1][d], qdr.T[d])
         if (~d).any():
-            assert_state_close(gq[t + 1][~d], pq[~d], f"{name} q step {t}")
-            assert_state_close(gqd[t + 1][~d], pqd[~d], f"{name} qd step {t}")
+            assert_state_close(gq[t + 1][~d], pq[~d], f"episodic {name} q step {t}", fq[~d])
+            assert_state_close(gqd[t + 1][~d], pqd[~d], f"episodic {name} qd step {t}", fqd[~d])
         e[d] = 0
     assert fired > 0
     np.testing.assert_array_equal(ep.cpu().numpy(), e)

@@ -98,3 +98,42 @@ def test_policy_window_graph_capture_replays_forward_and_backward():
         assert torch.allclose(loss_g, loss_ref, rtol=1e-6, atol=0)
         for a, b in zip(g_g, g_ref):
             assert torch.allclose(a, b, rtol=1e-5, atol=1e-9)
+
+
+def test_full_size_policy_window_gradient_on_sampled_environments(oracle_mod):
+    """512 environments, h = 8, the loss restricted to 4 sampled environments
+    by its per-environment weights (environments are independent, so dL/dtheta
+    is exactly their contribution): GPU autograd through the step adjoints
+    against the appendix A.1 recursion over the sampled environments."""
+    from paper_2204_07137_gb300.policy import free_root_observation, policy_window_loss
+    N, h = 512, 8
+    m, sim, pol, q0, qd0 = _setup(N, h, seed=2)
+    envs = np.sort(np.random.default_rng(5).choice(N, size=4, replace=False))
+    w = torch.zeros(N, device="cuda")
+    w[torch.from_numpy(envs).cuda()] = 1.0
+    keep = []
+    loss = policy_window_loss(sim, pol, q0, qd0, h, keep, env_weight=w)
+    loss.backward()
+    g_gpu = torch.cat([p.grad.reshape(-1) for p in pol.parameters()]).cpu().numpy()
+    assert np.isfinite(g_gpu).all() and np.abs(g_gpu).max() > 0
+    o = oracle_mod.Oracle(m)
+    pol64 = copy.deepcopy(pol).double().cpu()
+    params = list(pol64.parameters())
+    theta_bar = [torch.zeros_like(p) for p in params]
+    ne = len(envs)
+    qbar, qdbar = np.zeros((ne, m.nq)), np.zeros((ne, m.nv))
+    rbar = np.full(ne, -1.0 / (N * h))
+    for t in range(h - 1, -1, -1):
+        q, qd, a = (x.detach().cpu().numpy().astype(np.float64) for x in keep[t])
+        q, qd, a = q.reshape(m.nq, N)[:, envs], qd.reshape(m.nv, N)[:, envs], a.reshape(m.na, N)[:, envs]
+        sq, sqd, sa = o.step_vjp(q.T, qd.T, a.T, qbar, qdbar, rbar)
+        qt = torch.tensor(q, requires_grad=True)
+        qdt = torch.tensor(qd, requires_grad=True)
+        a64 = pol64(free_root_observation(qt, qdt))
+        grads = torch.autograd.grad(a64, [qt, qdt] + params, grad_outputs=torch.tensor(sa))
+        for k, gk in enumerate(grads[2:]):
+            theta_bar[k] += gk
+        qbar = sq + grads[0].numpy().T
+        qdbar = sqd + grads[1].numpy().T
+    g_ref = torch.cat([x.reshape(-1) for x in theta_bar]).numpy()
+    assert_grad_close(g_gpu[:, None], g_ref[:, None], "policy window dL/dtheta, 512 envs, 4 sampled", axis_env=-1)

@@ -770,7 +770,16 @@ def gradient_check(sim, groups, outf, outa, act, rbar, n_sample: int = 4):
         got = np.concatenate([g_a, gq_all[gi][:, envs].T, gqd_all[gi][:, envs].T], axis=1)
         ref = np.concatenate([ab.transpose(1, 0, 2).reshape(len(envs), -1), qb, qdb], axis=1)
         rel = np.linalg.norm(got - ref, axis=1) / np.linalg.norm(ref, axis=1)
-        out[f"{gi}:{model.name}"] = {"max": float(rel.max()), "envs": envs.tolist(), "rel": rel.tolist()}
+        # FP32 floor of each environment's gradient along the same checkpoints:
+        # the oracle's own deviation with every operation perturbed at FP32's
+        # unit roundoff (Monte Carlo Arithmetic, one run)
+        mc = o.mca_window_adjoint(qt.transpose(0, 2, 1), qdt.transpose(0, 2, 1), a.transpose(0, 2, 1), rb,
+                                  np.zeros((len(envs), model.nq)), np.zeros((len(envs), model.nv)), seed=11,
+                                  tangents=False)
+        mref = np.concatenate([mc[2].transpose(1, 0, 2).reshape(len(envs), -1), mc[0], mc[1]], axis=1)
+        floor = np.linalg.norm(mref - ref, axis=1) / np.linalg.norm(ref, axis=1)
+        out[f"{gi}:{model.name}"] = {"max": float(rel.max()), "envs": envs.tolist(), "rel": rel.tolist(),
+                                     "fp32_floor": floor.tolist()}
         off += N
     return out
 

@@ -17,7 +17,8 @@ struct shac_model {
   float h = 0, grav[3] = {0, 0, 0}, ke = 0, kd = 0, kt = 0, mu = 0, klim = 0, rc[10] = {0};
   int root_free = 0;
   int height_q = -1, vx_dof = -1;   // reward / termination coordinates (free root: 2 / world vx)
-  std::vector<int> parent, jtype, qs, ds, nd, lvl_ptr, lvl_link, ch_ptr, ch_idx, li_ptr, li_idx, dof_link, dof_k,
+  std::vector<int> parent, jtype, qs, ds, nd, lvl_ptr, lvl_link, ch_ptr, ch_idx, lc_ptr, lc_idx, lm_ptr, lm_idx, dof_link,
+      dof_k,
       dof_act, item_link, seg_mus, mus_seg_ptr, anc_mask, chain_tail;
   std::vector<float> axis, jpos, jrot, mass, com, icom, qlo, qhi, arm, damp, gear, item_pos, crad, fmax, rwq, rwqd;
   DevModel layout;   // sizes + scratch offsets (pointers unset)
@@ -82,18 +83,25 @@ static void compute_layout(shac_model* m) {
   const int L = m->L, nv = m->nv, ni = m->nitems;
   int o = 0;
   auto take = [&](int& off, int n) { off = o; o += n; };
-  // substep record: the start state and every forward intermediate the reverse pass reads
-  take(d.o_Q, m->nq); take(d.o_QD, nv); take(d.o_R, 9 * L); take(d.o_P, 3 * L); take(d.o_SI, 10 * L);
-  take(d.o_S, 6 * nv); take(d.o_V, 6 * L); take(d.o_FX, 6 * L); take(d.o_IT, 7 * ni);
+  // substep record: the start state and every forward intermediate the reverse
+  // pass reads (per link: pose, spatial inertia, velocity, external wrench)
+  take(d.o_Q, m->nq); take(d.o_QD, nv); take(d.o_LR, LREC * L);
+  take(d.o_S, 6 * nv); take(d.o_IT, 7 * ni);
   take(d.o_M, nv * nv); take(d.o_LD, nv); take(d.o_QDD, nv);
   o = (o + 3) / 4 * 4;   // records are copied 16 bytes at a time
   d.rec_floats = o;
   take(d.o_ACT, m->na); take(d.o_QB, m->nq); take(d.o_QDB, nv); take(d.o_ACTB, m->na);
-  take(d.o_QC, m->nq); take(d.o_QDC, nv); take(d.o_A, 6 * L); take(d.o_F, 6 * L); take(d.o_IC, 10 * L);
+  take(d.o_QC, m->nq); take(d.o_QDC, nv); take(d.o_LW, LWORK * L);
   take(d.o_B, nv); take(d.o_T, nv);
-  take(d.o_LAM, nv); take(d.o_VB, 6 * L); take(d.o_AB, 6 * L); take(d.o_FB, 6 * L);
-  take(d.o_RB, 9 * L); take(d.o_PB, 3 * L); take(d.o_ITB, 10 * ni); take(d.o_TP, 12 * L);
+  take(d.o_LAM, nv); take(d.o_ITB, 10 * ni);
   take(d.o_SEGA, m->nseg);
+  // free root: its six DOFs' reverse terms (velocity cotangent sums 6, then
+  // one rotation-column share of 3 per DOF)
+  take(d.o_RDB, m->root_free ? 24 : 0);
+  // partial muscle sums of (link, part) slots: at most max(32, L) slots (parts
+  // = lanes / links when a team has at least two lanes per link, else 1),
+  // 6 floats forward, 12 in reverse
+  take(d.o_MW, m->nseg > 0 ? std::max(32, L) * 12 : 0);
   d.env_floats = o;
 }
 
@@ -242,13 +250,17 @@ extern "C" shac_status shac_model_create(const shac_model_desc* dsc, shac_model*
   }
   m->mus_seg_ptr[m->nm] = m->nseg;
   m->nitems = m->nc + 2 * m->nseg;
-  m->li_ptr.assign(L + 1, 0);
+  // per-link lists of the contact items and of the muscle via-point items
+  m->lc_ptr.assign(L + 1, 0);
+  m->lm_ptr.assign(L + 1, 0);
   for (int i = 0; i < L; ++i) {
-    m->li_ptr[i] = (int)m->li_idx.size();
+    m->lc_ptr[i] = (int)m->lc_idx.size();
+    m->lm_ptr[i] = (int)m->lm_idx.size();
     for (int e = 0; e < m->nitems; ++e)
-      if (m->item_link[e] == i) m->li_idx.push_back(e);
+      if (m->item_link[e] == i) (e < m->nc ? m->lc_idx : m->lm_idx).push_back(e);
   }
-  m->li_ptr[L] = (int)m->li_idx.size();
+  m->lc_ptr[L] = (int)m->lc_idx.size();
+  m->lm_ptr[L] = (int)m->lm_idx.size();
   m->na = m->ntact + m->nm;
   m->K = dsc->substeps;
   m->h = (float)((double)dsc->dt / dsc->substeps);
@@ -292,7 +304,8 @@ static shac_status upload_model(const shac_model* m, Group& g) {
   };
   addi(&d.parent, m->parent); addi(&d.jtype, m->jtype); addi(&d.qs, m->qs); addi(&d.ds, m->ds); addi(&d.nd, m->nd);
   addi(&d.lvl_ptr, m->lvl_ptr); addi(&d.lvl_link, m->lvl_link); addi(&d.chain_tail, m->chain_tail); addi(&d.ch_ptr, m->ch_ptr); addi(&d.ch_idx, m->ch_idx);
-  addi(&d.li_ptr, m->li_ptr); addi(&d.li_idx, m->li_idx); addi(&d.dof_link, m->dof_link); addi(&d.dof_k, m->dof_k);
+  addi(&d.lc_ptr, m->lc_ptr); addi(&d.lc_idx, m->lc_idx); addi(&d.lm_ptr, m->lm_ptr); addi(&d.lm_idx, m->lm_idx);
+  addi(&d.dof_link, m->dof_link); addi(&d.dof_k, m->dof_k);
   addi(&d.dof_act, m->dof_act); addi(&d.item_link, m->item_link); addi(&d.seg_mus, m->seg_mus);
   addi(&d.mus_seg_ptr, m->mus_seg_ptr);
   {

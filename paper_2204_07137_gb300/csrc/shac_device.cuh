@@ -61,7 +61,8 @@ struct DevModel {
   const int *lvl_ptr, *lvl_link;         // chain heads grouped by chain depth
   const int *chain_tail;                 // last link of the chain starting at a head
   const int *ch_ptr, *ch_idx;            // children lists
-  const int *li_ptr, *li_idx;            // force items attached to each link
+  const int *lc_ptr, *lc_idx;            // contact items attached to each link
+  const int *lm_ptr, *lm_idx;            // muscle via-point items attached to each link
   const float *axis, *jpos, *jrot, *mass, *com, *icom;
   // dofs
   const int *dof_link, *dof_k, *dof_act;
@@ -76,12 +77,23 @@ struct DevModel {
   const float *rwq, *rwqd;
   // per-environment scratch layout (float offsets)
   int o_Q, o_QD, o_ACT, o_QB, o_QDB, o_ACTB;
-  int o_R, o_P, o_SI, o_S, o_V, o_A, o_F, o_FX, o_IT, o_IC, o_M, o_LD, o_B, o_T, o_QDD;
+  int o_LR, o_LW;                        // per-link records: LREC floats each (in the substep record), LWORK (work)
+  int o_S, o_IT, o_M, o_LD, o_B, o_T, o_QDD;
   int o_QC, o_QDC;                       // compensation (low parts) of q, qd within a step
-  int o_LAM, o_VB, o_AB, o_FB, o_RB, o_PB, o_ITB, o_TP, o_SEGA;
+  int o_LAM, o_ITB, o_SEGA, o_MW, o_RDB;
   int rec_floats;       // floats of the substep record: scratch [0, rec_floats) (o_Q first)
   int env_floats;
 };
+
+// Per-link scratch: two records per link with fields at fixed offsets, so a
+// pass over link i computes one base address per record.  The record part is
+// inside the substep record the reverse pass reloads; the work part holds the
+// recursions' intermediates and the reverse pass's cotangents.  Both strides
+// are odd, so the lanes of a one-lane-per-link pass hit distinct banks.
+constexpr int LREC = 35;    // R 9, P 3, spatial inertia 10, V 6, external wrench 6, pad
+constexpr int LR_R = 0, LR_P = 9, LR_SI = 12, LR_V = 22, LR_FX = 28;
+constexpr int LWORK = 65;   // A 6, F 6, Ic 10, V_bar 6, A_bar 6, F_bar 6, R_bar 9, P_bar 3, pose cotangent to parent 12, pad
+constexpr int LW_A = 0, LW_F = 6, LW_IC = 12, LW_VB = 22, LW_AB = 28, LW_FB = 34, LW_RB = 40, LW_PB = 49, LW_TP = 52;
 
 // ------------------------------------------------------------ accessors --
 // Global-memory scratch: component c of an environment at base[c * stride].
@@ -95,6 +107,9 @@ struct SMem {
   float* b;
   __device__ __forceinline__ float& operator[](int i) const { return b[i]; }
 };
+
+__device__ __forceinline__ int lrec(const DevModel& M, int i) { return M.o_LR + LREC * i; }
+__device__ __forceinline__ int lwork(const DevModel& M, int i) { return M.o_LW + LWORK * i; }
 
 __device__ __forceinline__ void team_sync(int nl) {
   if (nl > 1) __syncwarp();
@@ -236,8 +251,8 @@ template <class Mem>
 __device__ __forceinline__ void seg_forward(const DevModel& M, const Mem& w, int sg) {
   const int e0 = M.nc + 2 * sg, e1 = e0 + 1;
   const int l0 = __ldg(M.item_link + e0), l1 = __ldg(M.item_link + e1);
-  const V3 x0 = ld3(w, M.o_P + 3 * l0) + mul(ldm(w, M.o_R + 9 * l0), cld3(M.item_pos + 3 * e0));
-  const V3 x1 = ld3(w, M.o_P + 3 * l1) + mul(ldm(w, M.o_R + 9 * l1), cld3(M.item_pos + 3 * e1));
+  const V3 x0 = ld3(w, lrec(M, l0) + LR_P) + mul(ldm(w, lrec(M, l0) + LR_R), cld3(M.item_pos + 3 * e0));
+  const V3 x1 = ld3(w, lrec(M, l1) + LR_P) + mul(ldm(w, lrec(M, l1) + LR_R), cld3(M.item_pos + 3 * e1));
   const int mu_ = __ldg(M.seg_mus + sg);
   const float a = fminf(fmaxf(w[M.o_ACT + M.ntact + mu_], 0.f), 1.f);
   const float F = a * __ldg(M.fmax + mu_);
@@ -249,18 +264,22 @@ __device__ __forceinline__ void seg_forward(const DevModel& M, const Mem& w, int
   st3(w, M.o_IT + 7 * e1 + 3, -F * u);
 }
 
-// wrench of the muscle via points attached to link i
+// Wrench of part r (of parts) of the muscle via points attached to link i:
+// the link's items r, r + parts, r + 2 parts, ...
 template <class Mem>
-__device__ __forceinline__ void lk_muscle_wrench(const DevModel& M, const Mem& w, int i, V3& wn, V3& wf) {
+__device__ __forceinline__ void lk_muscle_wrench(const DevModel& M, const Mem& w, int i, int r, int parts, V3& wn,
+                                                 V3& wf) {
   wn = v3(0.f, 0.f, 0.f); wf = v3(0.f, 0.f, 0.f);
-  for (int k = __ldg(M.li_ptr + i); k < __ldg(M.li_ptr + i + 1); ++k) {
-    const int e = __ldg(M.li_idx + k);
-    if (e < M.nc) continue;
+  for (int k = __ldg(M.lm_ptr + i) + r; k < __ldg(M.lm_ptr + i + 1); k += parts) {
+    const int e = __ldg(M.lm_idx + k);
     const V3 x = ld3(w, M.o_IT + 7 * e), f = ld3(w, M.o_IT + 7 * e + 3);
     wn = wn + cross(x, f);
     wf = wf + f;
   }
 }
+
+// Lanes per link in the per-link muscle sums (at most 32 (link, part) slots).
+__device__ __forceinline__ int muscle_parts(const DevModel& M, int nl) { return nl >= 2 * M.L ? nl / M.L : 1; }
 
 // Tree sweeps visit chains: maximal runs of links in which every link but the
 // last has exactly one child.  A lane walks its chain parent-first (root-first
@@ -277,7 +296,7 @@ __device__ __forceinline__ int chain_next(const DevModel& M, int i) { return __l
 //
 // lk_joint_local: pose of link i in its parent's frame (joint frame times
 // joint motion: Rot(axis, q) for revolute, q axis for prismatic; the free
-// root's pose from its quaternion), written to o_R / o_P of link i.
+// root's pose from its quaternion), written to the pose fields of link i's record.
 template <class Mem>
 __device__ __forceinline__ void lk_joint_local(const DevModel& M, const Mem& w, int i) {
   const int jt = __ldg(M.jtype + i), s = __ldg(M.qs + i);
@@ -293,8 +312,8 @@ __device__ __forceinline__ void lk_joint_local(const DevModel& M, const Mem& w, 
     if (jt == J_REV) R = mul(R, axis_angle(ax, w[M.o_Q + s]));
     else if (jt == J_PRIS) P = P + w[M.o_Q + s] * mul(R, ax);
   }
-  stm(w, M.o_R + 9 * i, R);
-  st3(w, M.o_P + 3 * i, P);
+  stm(w, lrec(M, i) + LR_R, R);
+  st3(w, lrec(M, i) + LR_P, P);
 }
 
 // World pose, velocity and acceleration carried from a link to its child.
@@ -308,10 +327,10 @@ struct KinCarry {
 template <class Mem>
 __device__ __forceinline__ void kin_parent(const DevModel& M, const Mem& w, int p, KinCarry& c) {
   if (p >= 0) {
-    c.R = ldm(w, M.o_R + 9 * p);
-    c.P = ld3(w, M.o_P + 3 * p);
-    c.Vw = ld3(w, M.o_V + 6 * p); c.Vv = ld3(w, M.o_V + 6 * p + 3);
-    c.aw = ld3(w, M.o_A + 6 * p); c.av = ld3(w, M.o_A + 6 * p + 3);
+    c.R = ldm(w, lrec(M, p) + LR_R);
+    c.P = ld3(w, lrec(M, p) + LR_P);
+    c.Vw = ld3(w, lrec(M, p) + LR_V); c.Vv = ld3(w, lrec(M, p) + LR_V + 3);
+    c.aw = ld3(w, lwork(M, p) + LW_A); c.av = ld3(w, lwork(M, p) + LW_A + 3);
   } else {
     c.Vw = c.Vv = c.aw = v3(0.f, 0.f, 0.f);
     c.av = v3(-M.grav[0], -M.grav[1], -M.grav[2]);
@@ -329,8 +348,8 @@ __device__ __forceinline__ void lk_kin(const DevModel& M, const Mem& w, int i, K
   const int jt = __ldg(M.jtype + i), p = __ldg(M.parent + i);
   const int d0 = __ldg(M.ds + i), nd = __ldg(M.nd + i);
   const V3 ax = cld3(M.axis + 3 * i);
-  const M33 Rl = ldm(w, M.o_R + 9 * i);
-  const V3 Pl = ld3(w, M.o_P + 3 * i);
+  const M33 Rl = ldm(w, lrec(M, i) + LR_R);
+  const V3 Pl = ld3(w, lrec(M, i) + LR_P);
   float qdv[6];
   if (jt == J_FREE) {
 #pragma unroll
@@ -347,8 +366,8 @@ __device__ __forceinline__ void lk_kin(const DevModel& M, const Mem& w, int i, K
     R = mul(c.R, Rl);
     P = c.P + mul(c.R, Pl);
   }
-  stm(w, M.o_R + 9 * i, R);
-  st3(w, M.o_P + 3 * i, P);
+  stm(w, lrec(M, i) + LR_R, R);
+  st3(w, lrec(M, i) + LR_P, P);
   V3 uw = v3(0.f, 0.f, 0.f), uv = v3(0.f, 0.f, 0.f);
   auto subspace = [&](int k, V3 sw, V3 sv) {
     st3(w, M.o_S + 6 * (d0 + k), sw);
@@ -372,8 +391,8 @@ __device__ __forceinline__ void lk_kin(const DevModel& M, const Mem& w, int i, K
   const V3 Vw = c.Vw + uw, Vv = c.Vv + uv;
   const V3 aw = c.aw + cross(Vw, uw);
   const V3 av = c.av + cross(Vw, uv) + cross(Vv, uw);
-  st3(w, M.o_V + 6 * i, Vw); st3(w, M.o_V + 6 * i + 3, Vv);
-  st3(w, M.o_A + 6 * i, aw); st3(w, M.o_A + 6 * i + 3, av);
+  st3(w, lrec(M, i) + LR_V, Vw); st3(w, lrec(M, i) + LR_V + 3, Vv);
+  st3(w, lwork(M, i) + LW_A, aw); st3(w, lwork(M, i) + LW_A + 3, av);
   c.R = R; c.P = P; c.Vw = Vw; c.Vv = Vv; c.aw = aw; c.av = av;
 }
 
@@ -383,10 +402,10 @@ __device__ __forceinline__ void lk_kin(const DevModel& M, const Mem& w, int i, K
 // acceleration lk_kin stored.
 template <class Mem>
 __device__ __forceinline__ void lk_local(const DevModel& M, const Mem& w, int i) {
-  const M33 R = ldm(w, M.o_R + 9 * i);
-  const V3 P = ld3(w, M.o_P + 3 * i);
-  const V3 Vw = ld3(w, M.o_V + 6 * i), Vv = ld3(w, M.o_V + 6 * i + 3);
-  const V3 aw = ld3(w, M.o_A + 6 * i), av = ld3(w, M.o_A + 6 * i + 3);
+  const M33 R = ldm(w, lrec(M, i) + LR_R);
+  const V3 P = ld3(w, lrec(M, i) + LR_P);
+  const V3 Vw = ld3(w, lrec(M, i) + LR_V), Vv = ld3(w, lrec(M, i) + LR_V + 3);
+  const V3 aw = ld3(w, lwork(M, i) + LW_A), av = ld3(w, lwork(M, i) + LW_A + 3);
   const float m = __ldg(M.mass + i);
   const V3 c = P + mul(R, cld3(M.com + 3 * i));
   const M33 Iw = mulBT(mul(R, com_inertia(M, i)), R);
@@ -396,7 +415,7 @@ __device__ __forceinline__ void lk_local(const DevModel& M, const Mem& w, int i)
   const float izz = Iw.m[8] + m * (cc - c.z * c.z), ixy = Iw.m[1] - m * c.x * c.y;
   const float ixz = Iw.m[2] - m * c.x * c.z, iyz = Iw.m[5] - m * c.y * c.z;
   {
-    const int o = M.o_SI + 10 * i;
+    const int o = lrec(M, i) + LR_SI;
     w[o] = m; st3(w, o + 1, h);
     w[o + 4] = ixx; w[o + 5] = iyy; w[o + 6] = izz; w[o + 7] = ixy; w[o + 8] = ixz; w[o + 9] = iyz;
   }
@@ -410,12 +429,11 @@ __device__ __forceinline__ void lk_local(const DevModel& M, const Mem& w, int i)
   //   f_n = (-ke + kd ddot) min(d, 0),  d = height of x, ddot = v_x . n
   //   f_t = -v_t/|v_t| min(kt |v_t|, mu |f_n|)  (viscous branch when kt|v_t| <= mu|f_n|)
   V3 wn = v3(0.f, 0.f, 0.f), wf = v3(0.f, 0.f, 0.f);
-  const int k0 = __ldg(M.li_ptr + i), k1 = __ldg(M.li_ptr + i + 1);
+  const int k0 = __ldg(M.lc_ptr + i), k1 = __ldg(M.lc_ptr + i + 1);
   if (k0 != k1) {
     const float zroot = M.root_free ? w[M.o_Q + 2] : 0.f;
     for (int k = k0; k < k1; ++k) {
-      const int ci = __ldg(M.li_idx + k);
-      if (ci >= M.nc) continue;   // muscle via point
+      const int ci = __ldg(M.lc_idx + k);
       V3 x = P + mul(R, cld3(M.item_pos + 3 * ci));
       x.z -= __ldg(M.crad + ci);
       const float d = x.z + zroot;
@@ -436,15 +454,15 @@ __device__ __forceinline__ void lk_local(const DevModel& M, const Mem& w, int i)
       wf = wf + f;
     }
   }
-  st3(w, M.o_FX + 6 * i, wn);
-  st3(w, M.o_FX + 6 * i + 3, wf);
+  st3(w, lrec(M, i) + LR_FX, wn);
+  st3(w, lrec(M, i) + LR_FX + 3, wf);
   V3 fn, ff, bn, bf;
   imul(aw, av, fn, ff);
   imul(Vw, Vv, bn, bf);
   fn = fn + cross(Vw, bn) + cross(Vv, bf) - wn;
   ff = ff + cross(Vw, bf) - wf;
-  st3(w, M.o_F + 6 * i, fn);
-  st3(w, M.o_F + 6 * i + 3, ff);
+  st3(w, lwork(M, i) + LW_F, fn);
+  st3(w, lwork(M, i) + LW_F + 3, ff);
 }
 
 // Sweep 1: one lane per link the joint transforms; root first the world
@@ -472,13 +490,26 @@ __device__ void sw_forward(const DevModel& M, const Mem& w, int lane, int nl) {
   if (M.nseg > 0) {
     for (int sg = lane; sg < M.nseg; sg += nl) seg_forward(M, w, sg);
     team_sync(nl);
-    for (int i = lane; i < M.L; i += nl) {
+    // each link's muscle wrench in `parts` partial sums on as many lanes,
+    // then added in part order
+    const int parts = muscle_parts(M, nl);
+    for (int sl = lane; sl < M.L * parts; sl += nl) {
       V3 wn, wf;
-      lk_muscle_wrench(M, w, i, wn, wf);
-      add3(w, M.o_FX + 6 * i, wn);
-      add3(w, M.o_FX + 6 * i + 3, wf);
-      add3(w, M.o_F + 6 * i, -wn);
-      add3(w, M.o_F + 6 * i + 3, -wf);
+      lk_muscle_wrench(M, w, sl / parts, sl % parts, parts, wn, wf);
+      st3(w, M.o_MW + 6 * sl, wn);
+      st3(w, M.o_MW + 6 * sl + 3, wf);
+    }
+    team_sync(nl);
+    for (int i = lane; i < M.L; i += nl) {
+      V3 wn = v3(0.f, 0.f, 0.f), wf = v3(0.f, 0.f, 0.f);
+      for (int r = 0; r < parts; ++r) {
+        wn = wn + ld3(w, M.o_MW + 6 * (i * parts + r));
+        wf = wf + ld3(w, M.o_MW + 6 * (i * parts + r) + 3);
+      }
+      add3(w, lrec(M, i) + LR_FX, wn);
+      add3(w, lrec(M, i) + LR_FX + 3, wf);
+      add3(w, lwork(M, i) + LW_F, -wn);
+      add3(w, lwork(M, i) + LW_F + 3, -wf);
     }
     team_sync(nl);
   }
@@ -497,18 +528,18 @@ struct GatherCarry {
 // children from scratch.
 template <class Mem>
 __device__ __forceinline__ void lk_gather(const DevModel& M, const Mem& w, int i, bool tail, GatherCarry& g) {
-  V3 fn = ld3(w, M.o_F + 6 * i), ff = ld3(w, M.o_F + 6 * i + 3);
+  V3 fn = ld3(w, lwork(M, i) + LW_F), ff = ld3(w, lwork(M, i) + LW_F + 3);
   float ic[10];
 #pragma unroll
-  for (int k = 0; k < 10; ++k) ic[k] = w[M.o_SI + 10 * i + k];
+  for (int k = 0; k < 10; ++k) ic[k] = w[lrec(M, i) + LR_SI + k];
   if (tail) {
     const int c0 = __ldg(M.ch_ptr + i), c1 = __ldg(M.ch_ptr + i + 1);
     for (int kk = c0; kk < c1; ++kk) {
       const int c = __ldg(M.ch_idx + kk);
-      fn = fn + ld3(w, M.o_F + 6 * c);
-      ff = ff + ld3(w, M.o_F + 6 * c + 3);
+      fn = fn + ld3(w, lwork(M, c) + LW_F);
+      ff = ff + ld3(w, lwork(M, c) + LW_F + 3);
 #pragma unroll
-      for (int k = 0; k < 10; ++k) ic[k] += w[M.o_IC + 10 * c + k];
+      for (int k = 0; k < 10; ++k) ic[k] += w[lwork(M, c) + LW_IC + k];
     }
   } else {
     fn = fn + g.fn;
@@ -516,10 +547,10 @@ __device__ __forceinline__ void lk_gather(const DevModel& M, const Mem& w, int i
 #pragma unroll
     for (int k = 0; k < 10; ++k) ic[k] += g.ic[k];
   }
-  st3(w, M.o_F + 6 * i, fn);
-  st3(w, M.o_F + 6 * i + 3, ff);
+  st3(w, lwork(M, i) + LW_F, fn);
+  st3(w, lwork(M, i) + LW_F + 3, ff);
 #pragma unroll
-  for (int k = 0; k < 10; ++k) w[M.o_IC + 10 * i + k] = ic[k];
+  for (int k = 0; k < 10; ++k) w[lwork(M, i) + LW_IC + k] = ic[k];
   g.fn = fn;
   g.ff = ff;
 #pragma unroll
@@ -562,8 +593,8 @@ __device__ __forceinline__ float joint_force(const DevModel& M, const Mem& w, in
 template <class Mem>
 __device__ __forceinline__ float dof_rhs(const DevModel& M, const Mem& w, int d) {
   const int i = __ldg(M.dof_link + d);
-  const float c = dot(ld3(w, M.o_S + 6 * d), ld3(w, M.o_F + 6 * i)) +
-                  dot(ld3(w, M.o_S + 6 * d + 3), ld3(w, M.o_F + 6 * i + 3));
+  const float c = dot(ld3(w, M.o_S + 6 * d), ld3(w, lwork(M, i) + LW_F)) +
+                  dot(ld3(w, M.o_S + 6 * d + 3), ld3(w, lwork(M, i) + LW_F + 3));
   return joint_force(M, w, d) - c;
 }
 
@@ -583,7 +614,7 @@ __device__ void st_mass_rows(const DevModel& M, const Mem& w, int lane, int nl) 
     const int i = __ldg(M.dof_link + a);
     for (int b = 0; b < a; ++b) w[M.o_M + a * n + b] = 0.f;
     V3 fn, ff;
-    si_mul(w, M.o_IC + 10 * i, ld3(w, M.o_S + 6 * a), ld3(w, M.o_S + 6 * a + 3), fn, ff);
+    si_mul(w, lwork(M, i) + LW_IC, ld3(w, M.o_S + 6 * a), ld3(w, M.o_S + 6 * a + 3), fn, ff);
     for (int j = i; j >= 0; j = __ldg(M.parent + j)) {
       const int b0 = __ldg(M.ds + j), nb = __ldg(M.nd + j);
       for (int b = b0; b < b0 + nb && b <= a; ++b)
@@ -656,7 +687,7 @@ __device__ __forceinline__ void lk_integrate(const DevModel& M, const Mem& w, in
     w[M.o_QDC + d] = e;
   }
   if (jt == J_FREE) {
-    const M33 R = ldm(w, M.o_R + 9 * i);
+    const M33 R = ldm(w, lrec(M, i) + LR_R);
     const V3 dp = M.h * mul(R, ld3(w, M.o_QD + d0 + 3)) + M.h * mul(R, ld3(w, M.o_QDC + d0 + 3));
     float e;
     w[M.o_Q + s] = two_sum(w[M.o_Q + s], dp.x + w[M.o_QC + s], e); w[M.o_QC + s] = e;
@@ -767,8 +798,10 @@ __device__ __forceinline__ void bsub(const DevModel& M, const Mem& w, float inv_
 template <int B, int NM, class Mem>
 __device__ __forceinline__ void row_entry(const DevModel& M, const Mem& w, float (&row)[NM], unsigned mask, V3 fn,
                                           V3 ff, float arm, int lane) {
-  float v = 0.f;
-  if ((mask >> B) & 1u) v = dot(ld3(w, M.o_S + 6 * B), fn) + dot(ld3(w, M.o_S + 6 * B + 3), ff);
+  // every lane reads column B's subspace (a broadcast; padding columns read
+  // other scratch) and keeps the product only where DOF B moves an ancestor
+  const float p = dot(ld3(w, M.o_S + 6 * B), fn) + dot(ld3(w, M.o_S + 6 * B + 3), ff);
+  float v = ((mask >> B) & 1u) ? p : 0.f;
   if (B == lane) v += arm;
   row[B] = v;
 }
@@ -780,7 +813,7 @@ __device__ __forceinline__ void row_assemble(const DevModel& M, const Mem& w, fl
   const bool own = lane < M.nv;
   if (own) {
     const int i = __ldg(M.dof_link + lane);
-    si_mul(w, M.o_IC + 10 * i, ld3(w, M.o_S + 6 * lane), ld3(w, M.o_S + 6 * lane + 3), fn, ff);
+    si_mul(w, lwork(M, i) + LW_IC, ld3(w, M.o_S + 6 * lane), ld3(w, M.o_S + 6 * lane + 3), fn, ff);
     mask = __ldg(M.anc_mask + lane);
   }
   const float arm = own ? __ldg(M.arm + lane) : 1.f;
@@ -949,7 +982,7 @@ __device__ __forceinline__ void zero_range(const Mem& w, int o, int n, int lane,
 // ================================================================= ADJOINT ==
 
 // Reverse of lk_integrate for link i.  Inputs: o_Q/o_QD hold the substep
-// START state, o_QDD its accelerations, o_R its rotations; o_QB/o_QDB hold the
+// START state, o_QDD its accelerations, the link records its rotations; o_QB/o_QDB hold the
 // cotangents of the substep END state.  Outputs (link i's entries): o_QB/o_QDB
 // partial cotangents of the start state (integrator paths only) and
 // o_T = qdd_bar.
@@ -960,7 +993,7 @@ __device__ __forceinline__ void lk_integrate_adj(const DevModel& M, const Mem& w
   if (jt == J_REV || jt == J_PRIS) {
     w[M.o_QDB + d] += h * w[M.o_QB + s];          // q' = q + h qd'
   } else if (jt == J_FREE) {
-    const M33 R = ldm(w, M.o_R + 9 * i);
+    const M33 R = ldm(w, lrec(M, i) + LR_R);
     const V3 vb1 = ld3(w, M.o_QD + d + 3) + h * ld3(w, M.o_QDD + d + 3);   // new body velocity
     const V3 om1 = ld3(w, M.o_QD + d) + h * ld3(w, M.o_QDD + d);
     const V3 pb = ld3(w, M.o_QB + s);
@@ -1021,8 +1054,8 @@ struct AccCarry {
 template <class Mem>
 __device__ __forceinline__ void acc_parent(const DevModel& M, const Mem& w, int p, AccCarry& c) {
   if (p >= 0) {
-    c.aw = ld3(w, M.o_A + 6 * p); c.av = ld3(w, M.o_A + 6 * p + 3);
-    c.nb = ld3(w, M.o_FB + 6 * p); c.fb = ld3(w, M.o_FB + 6 * p + 3);
+    c.aw = ld3(w, lwork(M, p) + LW_A); c.av = ld3(w, lwork(M, p) + LW_A + 3);
+    c.nb = ld3(w, lwork(M, p) + LW_FB); c.fb = ld3(w, lwork(M, p) + LW_FB + 3);
   } else {
     c.aw = c.nb = c.fb = v3(0.f, 0.f, 0.f);
     c.av = v3(-M.grav[0], -M.grav[1], -M.grav[2]);
@@ -1031,7 +1064,7 @@ __device__ __forceinline__ void acc_parent(const DevModel& M, const Mem& w, int 
 template <class Mem>
 __device__ __forceinline__ void lk_adj_acc(const DevModel& M, const Mem& w, int i, AccCarry& c) {
   const int d0 = __ldg(M.ds + i), nd = __ldg(M.nd + i);
-  const V3 Vw = ld3(w, M.o_V + 6 * i), Vv = ld3(w, M.o_V + 6 * i + 3);
+  const V3 Vw = ld3(w, lrec(M, i) + LR_V), Vv = ld3(w, lrec(M, i) + LR_V + 3);
   V3 aw = c.aw, av = c.av, nb = c.nb, fb = c.fb;
   V3 uw = v3(0.f, 0.f, 0.f), uv = v3(0.f, 0.f, 0.f);
   for (int d = d0; d < d0 + nd; ++d) {
@@ -1043,8 +1076,8 @@ __device__ __forceinline__ void lk_adj_acc(const DevModel& M, const Mem& w, int 
   }
   aw = aw + cross(Vw, uw);
   av = av + cross(Vw, uv) + cross(Vv, uw);
-  st3(w, M.o_A + 6 * i, aw); st3(w, M.o_A + 6 * i + 3, av);
-  st3(w, M.o_FB + 6 * i, nb); st3(w, M.o_FB + 6 * i + 3, fb);
+  st3(w, lwork(M, i) + LW_A, aw); st3(w, lwork(M, i) + LW_A + 3, av);
+  st3(w, lwork(M, i) + LW_FB, nb); st3(w, lwork(M, i) + LW_FB + 3, fb);
   c.aw = aw; c.av = av; c.nb = nb; c.fb = fb;
 }
 
@@ -1083,7 +1116,7 @@ __device__ __forceinline__ void dof_adj_force(const DevModel& M, const Mem& w, i
 template <class Mem>
 __device__ __forceinline__ void lk_adj_local(const DevModel& M, const Mem& w, int i) {
   const int jt = __ldg(M.jtype + i);
-  const int osi = M.o_SI + 10 * i;
+  const int osi = lrec(M, i) + LR_SI;
   const float m = w[osi];
   const V3 h = ld3(w, osi + 1);
   const float ixx = w[osi + 4], iyy = w[osi + 5], izz = w[osi + 6], ixy = w[osi + 7], ixz = w[osi + 8],
@@ -1093,22 +1126,22 @@ __device__ __forceinline__ void lk_adj_local(const DevModel& M, const Mem& w, in
             ixz * xw.x + iyz * xw.y + izz * xw.z) + cross(h, xv);
     yf = m * xv - cross(h, xw);
   };
-  const V3 Vw = ld3(w, M.o_V + 6 * i), Vv = ld3(w, M.o_V + 6 * i + 3);
-  const V3 aw = ld3(w, M.o_A + 6 * i), av = ld3(w, M.o_A + 6 * i + 3);
-  const V3 nb = ld3(w, M.o_FB + 6 * i), fb = ld3(w, M.o_FB + 6 * i + 3);
+  const V3 Vw = ld3(w, lrec(M, i) + LR_V), Vv = ld3(w, lrec(M, i) + LR_V + 3);
+  const V3 aw = ld3(w, lwork(M, i) + LW_A), av = ld3(w, lwork(M, i) + LW_A + 3);
+  const V3 nb = ld3(w, lwork(M, i) + LW_FB), fb = ld3(w, lwork(M, i) + LW_FB + 3);
   {
     V3 fn, ff, bn, bf;
     imul(aw, av, fn, ff);
     imul(Vw, Vv, bn, bf);
-    fn = fn + cross(Vw, bn) + cross(Vv, bf) - ld3(w, M.o_FX + 6 * i);
-    ff = ff + cross(Vw, bf) - ld3(w, M.o_FX + 6 * i + 3);
-    st3(w, M.o_F + 6 * i, fn); st3(w, M.o_F + 6 * i + 3, ff);
+    fn = fn + cross(Vw, bn) + cross(Vv, bf) - ld3(w, lrec(M, i) + LR_FX);
+    ff = ff + cross(Vw, bf) - ld3(w, lrec(M, i) + LR_FX + 3);
+    st3(w, lwork(M, i) + LW_F, fn); st3(w, lwork(M, i) + LW_F + 3, ff);
   }
   // A_bar = I F_bar (I symmetric)
   V3 abn, abf;
   imul(nb, fb, abn, abf);
-  st3(w, M.o_AB + 6 * i, abn);
-  st3(w, M.o_AB + 6 * i + 3, abf);
+  st3(w, lwork(M, i) + LW_AB, abn);
+  st3(w, lwork(M, i) + LW_AB + 3, abf);
   V3 hb = v3(0.f, 0.f, 0.f);
   M33 G;
 #pragma unroll
@@ -1127,8 +1160,8 @@ __device__ __forceinline__ void lk_adj_local(const DevModel& M, const Mem& w, in
   vvb = vvb + t2;
   si_adj(hb, G, Vw, Vv, Bnb, Bfb);
   // spatial inertia about the reference point -> pose cotangents
-  const M33 R = ldm(w, M.o_R + 9 * i);
-  const V3 P = ld3(w, M.o_P + 3 * i);
+  const M33 R = ldm(w, lrec(M, i) + LR_R);
+  const V3 P = ld3(w, lrec(M, i) + LR_P);
   V3 Pb = v3(0.f, 0.f, 0.f);
   M33 Rb;
 #pragma unroll
@@ -1148,10 +1181,9 @@ __device__ __forceinline__ void lk_adj_local(const DevModel& M, const Mem& w, in
     add_outer(Rb, cb, com);
   }
   // contacts of link i: Fext cotangent = -F_bar
-  const int k0 = __ldg(M.li_ptr + i), k1 = __ldg(M.li_ptr + i + 1);
+  const int k0 = __ldg(M.lc_ptr + i), k1 = __ldg(M.lc_ptr + i + 1);
   for (int k = k0; k < k1; ++k) {
-    const int c = __ldg(M.li_idx + k);
-    if (c >= M.nc) continue;
+    const int c = __ldg(M.lc_idx + k);
     const float dep = w[M.o_IT + 7 * c + 6];
     float db = 0.f;
     if (dep < 0.f) {
@@ -1190,14 +1222,14 @@ __device__ __forceinline__ void lk_adj_local(const DevModel& M, const Mem& w, in
     }
     w[M.o_ITB + 10 * c + 9] = db;
   }
-  st3(w, M.o_VB + 6 * i, vwb);
-  st3(w, M.o_VB + 6 * i + 3, vvb);
-  st3(w, M.o_PB + 3 * i, Pb);
-  stm(w, M.o_RB + 9 * i, Rb);
+  st3(w, lwork(M, i) + LW_VB, vwb);
+  st3(w, lwork(M, i) + LW_VB + 3, vvb);
+  st3(w, lwork(M, i) + LW_PB, Pb);
+  stm(w, lwork(M, i) + LW_RB, Rb);
   // joint-local rotation R_local = jrot Rot(axis, q) of a revolute joint with
-  // a parent, kept in o_TP of link i until the leaves-first sweep replaces it
+  // a parent, kept in link i's pose-cotangent slot until the leaves-first sweep replaces it
   if (jt == J_REV && __ldg(M.parent + i) >= 0)
-    stm(w, M.o_TP + 12 * i, mul(cldm(M.jrot + 9 * i), axis_angle(cld3(M.axis + 3 * i), w[M.o_Q + __ldg(M.qs + i)])));
+    stm(w, lwork(M, i) + LW_TP, mul(cldm(M.jrot + 9 * i), axis_angle(cld3(M.axis + 3 * i), w[M.o_Q + __ldg(M.qs + i)])));
 }
 
 // Reverse of one muscle segment: cotangents of both via points and of the
@@ -1208,8 +1240,8 @@ __device__ __forceinline__ void seg_adjoint(const DevModel& M, const Mem& w, int
   const int l0 = __ldg(M.item_link + e0), l1 = __ldg(M.item_link + e1);
   const V3 x0 = ld3(w, M.o_IT + 7 * e0), f0 = ld3(w, M.o_IT + 7 * e0 + 3);
   const V3 x1 = ld3(w, M.o_IT + 7 * e1), f1 = ld3(w, M.o_IT + 7 * e1 + 3);
-  const V3 n0b = -ld3(w, M.o_FB + 6 * l0), f0eb = -ld3(w, M.o_FB + 6 * l0 + 3);
-  const V3 n1b = -ld3(w, M.o_FB + 6 * l1), f1eb = -ld3(w, M.o_FB + 6 * l1 + 3);
+  const V3 n0b = -ld3(w, lwork(M, l0) + LW_FB), f0eb = -ld3(w, lwork(M, l0) + LW_FB + 3);
+  const V3 n1b = -ld3(w, lwork(M, l1) + LW_FB), f1eb = -ld3(w, lwork(M, l1) + LW_FB + 3);
   const V3 f0b = cross(n0b, x0) + f0eb, f1b = cross(n1b, x1) + f1eb;
   V3 x0b = cross(f0, n0b), x1b = cross(f1, n1b);
   const int mu_ = __ldg(M.seg_mus + sg);
@@ -1233,7 +1265,7 @@ __device__ __forceinline__ void seg_adjoint(const DevModel& M, const Mem& w, int
 
 // Children's contributions carried up a chain in registers: subtree sums of
 // the total force and of A_bar, the child's V_bar and its cotangent of this
-// link's pose (what o_TP holds for a chain head).
+// link's pose (what the pose-cotangent slot holds for a chain head).
 struct BwdCarry {
   V3 Fn, Ff, an, af, vw, vv, tP;
   M33 tR;
@@ -1244,30 +1276,30 @@ struct BwdCarry {
 // is the link walked before, carried in g), reverse the Newton-Euler
 // accelerations and velocities and the motion subspaces, and pass the pose
 // cotangent through the joint transform to the parent (R_p_bar, P_p_bar in
-// o_TP).  The inertia's share of the pose cotangents was added by
+// the pose-cotangent slot).  The inertia's share of the pose cotangents was added by
 // lk_adj_local; the joint's own q_bar is taken after the sweep (lk_adj_qbar)
-// from the final R_bar, P_bar left in o_RB, o_PB.
+// from the final R_bar, P_bar left in its work record.
 template <class Mem>
 __device__ __forceinline__ void lk_adj_bwd(const DevModel& M, const Mem& w, int i, bool tail, BwdCarry& g) {
-  V3 Fn = ld3(w, M.o_F + 6 * i), Ff = ld3(w, M.o_F + 6 * i + 3);
-  V3 an = ld3(w, M.o_AB + 6 * i), af = ld3(w, M.o_AB + 6 * i + 3);
-  V3 vw = ld3(w, M.o_VB + 6 * i), vv = ld3(w, M.o_VB + 6 * i + 3);
-  M33 Rb = ldm(w, M.o_RB + 9 * i);
-  V3 Pb = ld3(w, M.o_PB + 3 * i);
+  V3 Fn = ld3(w, lwork(M, i) + LW_F), Ff = ld3(w, lwork(M, i) + LW_F + 3);
+  V3 an = ld3(w, lwork(M, i) + LW_AB), af = ld3(w, lwork(M, i) + LW_AB + 3);
+  V3 vw = ld3(w, lwork(M, i) + LW_VB), vv = ld3(w, lwork(M, i) + LW_VB + 3);
+  M33 Rb = ldm(w, lwork(M, i) + LW_RB);
+  V3 Pb = ld3(w, lwork(M, i) + LW_PB);
   V3 cvw = v3(0.f, 0.f, 0.f), cvv = v3(0.f, 0.f, 0.f);
   if (tail) {
     const int c0 = __ldg(M.ch_ptr + i), c1 = __ldg(M.ch_ptr + i + 1);
     for (int k = c0; k < c1; ++k) {
       const int c = __ldg(M.ch_idx + k);
-      Fn = Fn + ld3(w, M.o_F + 6 * c);
-      Ff = Ff + ld3(w, M.o_F + 6 * c + 3);
-      an = an + ld3(w, M.o_AB + 6 * c);
-      af = af + ld3(w, M.o_AB + 6 * c + 3);
-      cvw = cvw + ld3(w, M.o_VB + 6 * c);
-      cvv = cvv + ld3(w, M.o_VB + 6 * c + 3);
+      Fn = Fn + ld3(w, lwork(M, c) + LW_F);
+      Ff = Ff + ld3(w, lwork(M, c) + LW_F + 3);
+      an = an + ld3(w, lwork(M, c) + LW_AB);
+      af = af + ld3(w, lwork(M, c) + LW_AB + 3);
+      cvw = cvw + ld3(w, lwork(M, c) + LW_VB);
+      cvv = cvv + ld3(w, lwork(M, c) + LW_VB + 3);
 #pragma unroll
-      for (int t = 0; t < 9; ++t) Rb.m[t] += w[M.o_TP + 12 * c + t];
-      Pb = Pb + ld3(w, M.o_TP + 12 * c + 9);
+      for (int t = 0; t < 9; ++t) Rb.m[t] += w[lwork(M, c) + LW_TP + t];
+      Pb = Pb + ld3(w, lwork(M, c) + LW_TP + 9);
     }
   } else {
     Fn = Fn + g.Fn; Ff = Ff + g.Ff;
@@ -1280,58 +1312,38 @@ __device__ __forceinline__ void lk_adj_bwd(const DevModel& M, const Mem& w, int 
   // the rest of link i's scratch reads come before its first store
   V3 uw, uv;
   joint_vel(M, w, i, uw, uv);
-  const V3 Vw = ld3(w, M.o_V + 6 * i), Vv = ld3(w, M.o_V + 6 * i + 3);
-  const M33 R = ldm(w, M.o_R + 9 * i);
-  const V3 P = ld3(w, M.o_P + 3 * i);
+  const V3 Vw = ld3(w, lrec(M, i) + LR_V), Vv = ld3(w, lrec(M, i) + LR_V + 3);
+  const M33 R = ldm(w, lrec(M, i) + LR_R);
+  const V3 P = ld3(w, lrec(M, i) + LR_P);
   const int jt = __ldg(M.jtype + i), d0 = __ldg(M.ds + i), nd = __ldg(M.nd + i);
   const int p = __ldg(M.parent + i);
-  M33 Rloc;   // joint-local rotation kept in o_TP by lk_adj_local (revolute with a parent)
-  if (jt == J_REV && p >= 0) Rloc = ldm(w, M.o_TP + 12 * i);
+  M33 Rloc;   // joint-local rotation kept in the pose-cotangent slot by lk_adj_local (revolute with a parent)
+  if (jt == J_REV && p >= 0) Rloc = ldm(w, lwork(M, i) + LW_TP);
   float lam1 = 0.f, qdd1 = 0.f, qd1 = 0.f, qdb1 = 0.f;   // a one-DOF joint's terms
   V3 s1w = v3(0.f, 0.f, 0.f), s1v = v3(0.f, 0.f, 0.f);
   if (jt != J_FREE && nd == 1) {
     lam1 = w[M.o_LAM + d0]; qdd1 = w[M.o_QDD + d0]; qd1 = w[M.o_QD + d0]; qdb1 = w[M.o_QDB + d0];
     s1w = ld3(w, M.o_S + 6 * d0); s1v = ld3(w, M.o_S + 6 * d0 + 3);
   }
-  st3(w, M.o_F + 6 * i, Fn);
-  st3(w, M.o_F + 6 * i + 3, Ff);
-  st3(w, M.o_AB + 6 * i, an);
-  st3(w, M.o_AB + 6 * i + 3, af);
+  st3(w, lwork(M, i) + LW_F, Fn);
+  st3(w, lwork(M, i) + LW_F + 3, Ff);
+  st3(w, lwork(M, i) + LW_AB, an);
+  st3(w, lwork(M, i) + LW_AB + 3, af);
   // A_i = A_p + sum S qdd + V_i x u_i
   vw = vw + cross(uw, an) + cross(uv, af) + cvw;
   vv = vv + cross(uw, af) + cvv;
-  st3(w, M.o_VB + 6 * i, vw);
-  st3(w, M.o_VB + 6 * i + 3, vv);
+  st3(w, lwork(M, i) + LW_VB, vw);
+  st3(w, lwork(M, i) + LW_VB + 3, vv);
   const V3 ubw = cross(an, Vw) + cross(af, Vv);
   const V3 ubv = cross(af, Vw);
   // motion subspaces of the DOFs of i: tau = S^T F_total, A and V terms
   const V3 ax = cld3(M.axis + 3 * i);
-  // per DOF: tau = S^T F_total gives qd_bar and the subspace cotangents
-  // (sbw, sbv); DOF counts are fixed by the joint type, so the column index
-  // of a free joint is a compile-time constant
-  auto dof_terms = [&](int k, V3& sbw, V3& sbv) {
-    const int d = d0 + k;
-    const float wd = -w[M.o_LAM + d], qdd = w[M.o_QDD + d], qd = w[M.o_QD + d];
-    const V3 sw = ld3(w, M.o_S + 6 * d), sv = ld3(w, M.o_S + 6 * d + 3);
-    w[M.o_QDB + d] += dot(sw, ubw + vw) + dot(sv, ubv + vv);
-    sbw = wd * Fn + qdd * an + qd * (ubw + vw);
-    sbv = wd * Ff + qdd * af + qd * (ubv + vv);
-  };
   if (jt == J_FREE) {
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {   // (R e_k, P x R e_k)
-      V3 sbw, sbv;
-      dof_terms(k, sbw, sbv);
-      const V3 rb = sbw + cross(sbv, P);
-      Pb = Pb + cross(col(R, k), sbv);
-      Rb.m[k] += rb.x; Rb.m[3 + k] += rb.y; Rb.m[6 + k] += rb.z;
-    }
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {   // (0, R e_k)
-      V3 sbw, sbv;
-      dof_terms(3 + k, sbw, sbv);
-      Rb.m[k] += sbv.x; Rb.m[3 + k] += sbv.y; Rb.m[6 + k] += sbv.z;
-    }
+    // a free joint is the root: its six DOF terms feed only its own q_bar, so
+    // they run after the sweep, one DOF per lane (root_dof_terms); keep the
+    // velocity cotangent sums they need
+    st3(w, M.o_RDB, ubw + vw);
+    st3(w, M.o_RDB + 3, ubv + vv);
   } else if (nd == 1) {
     const float wd = -lam1;
     w[M.o_QDB + d0] = qdb1 + (dot(s1w, ubw + vw) + dot(s1v, ubv + vv));
@@ -1347,8 +1359,8 @@ __device__ __forceinline__ void lk_adj_bwd(const DevModel& M, const Mem& w, int 
     }
     add_outer(Rb, ab, ax);
   }
-  stm(w, M.o_RB + 9 * i, Rb);
-  st3(w, M.o_PB + 3 * i, Pb);
+  stm(w, lwork(M, i) + LW_RB, Rb);
+  st3(w, lwork(M, i) + LW_PB, Pb);
   g.Fn = Fn; g.Ff = Ff; g.an = an; g.af = af; g.vw = vw; g.vv = vv;
   if (p >= 0 && jt != J_FREE) {
     // Rj = Rp jrot (joint frame in world), R = Rj Rot(ax, q), Pj = Pp + Rp jpos
@@ -1361,11 +1373,29 @@ __device__ __forceinline__ void lk_adj_bwd(const DevModel& M, const Mem& w, int 
       tp = mulBT(Rjb, cldm(M.jrot + 9 * i));
     }
     add_outer(tp, Pb, cld3(M.jpos + 3 * i));
-    stm(w, M.o_TP + 12 * i, tp);
-    st3(w, M.o_TP + 12 * i + 9, Pb);
+    stm(w, lwork(M, i) + LW_TP, tp);
+    st3(w, lwork(M, i) + LW_TP + 9, Pb);
     g.tR = tp;
     g.tP = Pb;
   }
+}
+
+// The free root's DOF d (0..5) after the leaves-first sweep: tau = S^T F_total
+// gives qd_bar_d and the subspace cotangents (sbw, sbv), whose share of the
+// root's rotation cotangent (column d mod 3: (R e_k, P x R e_k) for the body
+// rates, (0, R e_k) for v_body) is kept in o_RDB for lk_adj_qbar.  The root's
+// position cotangent is not needed (the root origin is the reference point).
+template <class Mem>
+__device__ __forceinline__ void root_dof_terms(const DevModel& M, const Mem& w, int d) {
+  const V3 uw = ld3(w, M.o_RDB), uv = ld3(w, M.o_RDB + 3);
+  const V3 Fn = ld3(w, lwork(M, 0) + LW_F), Ff = ld3(w, lwork(M, 0) + LW_F + 3);
+  const V3 an = ld3(w, lwork(M, 0) + LW_AB), af = ld3(w, lwork(M, 0) + LW_AB + 3);
+  const float wd = -w[M.o_LAM + d], qdd = w[M.o_QDD + d], qd = w[M.o_QD + d];
+  const V3 sw = ld3(w, M.o_S + 6 * d), sv = ld3(w, M.o_S + 6 * d + 3);
+  w[M.o_QDB + d] += dot(sw, uw) + dot(sv, uv);
+  const V3 sbw = wd * Fn + qdd * an + qd * uw;
+  const V3 sbv = wd * Ff + qdd * af + qd * uv;
+  st3(w, M.o_RDB + 6 + 3 * d, d < 3 ? sbw + cross(sbv, ld3(w, lrec(M, 0) + LR_P)) : sbv);
 }
 
 // q_bar of link i's joint from its final pose cotangents: revolute
@@ -1375,8 +1405,14 @@ __device__ __forceinline__ void lk_adj_bwd(const DevModel& M, const Mem& w, int 
 template <class Mem>
 __device__ __forceinline__ void lk_adj_qbar(const DevModel& M, const Mem& w, int i) {
   const int jt = __ldg(M.jtype + i), s = __ldg(M.qs + i);
-  const M33 Rb = ldm(w, M.o_RB + 9 * i);
+  M33 Rb = ldm(w, lwork(M, i) + LW_RB);
   if (jt == J_FREE) {   // the root origin is the reference point: no position cotangent here
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {   // the six DOF terms' shares, column k from DOFs k and 3 + k
+      const V3 a = ld3(w, M.o_RDB + 6 + 3 * k), b = ld3(w, M.o_RDB + 6 + 3 * (3 + k));
+      Rb.m[k] += a.x; Rb.m[3 + k] += a.y; Rb.m[6 + k] += a.z;
+      Rb.m[k] += b.x; Rb.m[3 + k] += b.y; Rb.m[6 + k] += b.z;
+    }
     float xb = 0.f, yb = 0.f, zb = 0.f, wb = 0.f;
     quat_to_R_adj(w[M.o_Q + s + 3], w[M.o_Q + s + 4], w[M.o_Q + s + 5], w[M.o_Q + s + 6], Rb, xb, yb, zb, wb);
     w[M.o_QB + s + 3] += xb; w[M.o_QB + s + 4] += yb; w[M.o_QB + s + 5] += zb; w[M.o_QB + s + 6] += wb;
@@ -1386,7 +1422,7 @@ __device__ __forceinline__ void lk_adj_qbar(const DevModel& M, const Mem& w, int
       w[M.o_QB + 2] += sd;
     }
   } else if (jt == J_REV) {
-    const M33 R = ldm(w, M.o_R + 9 * i);
+    const M33 R = ldm(w, lrec(M, i) + LR_R);
     const V3 a = mul(R, cld3(M.axis + 3 * i));
     float qb = 0.f;
 #pragma unroll
@@ -1396,8 +1432,8 @@ __device__ __forceinline__ void lk_adj_qbar(const DevModel& M, const Mem& w, int
     }
     w[M.o_QB + s] += qb;
   } else if (jt == J_PRIS) {
-    const M33 R = ldm(w, M.o_R + 9 * i);
-    w[M.o_QB + s] += dot(ld3(w, M.o_PB + 3 * i), mul(R, cld3(M.axis + 3 * i)));
+    const M33 R = ldm(w, lrec(M, i) + LR_R);
+    w[M.o_QB + s] += dot(ld3(w, lwork(M, i) + LW_PB), mul(R, cld3(M.axis + 3 * i)));
   }
 }
 
@@ -1438,21 +1474,39 @@ __device__ __forceinline__ void st_dynamics_adj(const DevModel& M, const Mem& w,
       for (int sg = __ldg(M.mus_seg_ptr + mu_); sg < __ldg(M.mus_seg_ptr + mu_ + 1); ++sg) sa += w[M.o_SEGA + sg];
       w[M.o_ACTB + M.ntact + mu_] += sa;
     }
+    // each link's via-point pose cotangents in `parts` partial sums, then
+    // added in part order
+    const int parts = muscle_parts(M, nl);
+    for (int sl = lane; sl < M.L * parts; sl += nl) {
+      const int i = sl / parts, r = sl % parts;
+      V3 Pb = v3(0.f, 0.f, 0.f);
+      M33 Rb;
+#pragma unroll
+      for (int k = 0; k < 9; ++k) Rb.m[k] = 0.f;
+      for (int k = __ldg(M.lm_ptr + i) + r; k < __ldg(M.lm_ptr + i + 1); k += parts) {
+        const int e = __ldg(M.lm_idx + k);
+        const V3 xb = ld3(w, M.o_ITB + 10 * e);
+        Pb = Pb + xb;
+        add_outer(Rb, xb, cld3(M.item_pos + 3 * e));
+      }
+      st3(w, M.o_MW + 12 * sl, Pb);
+      stm(w, M.o_MW + 12 * sl + 3, Rb);
+    }
+    team_sync(nl);
     for (int i = lane; i < M.L; i += nl) {
       V3 Pb = v3(0.f, 0.f, 0.f);
       M33 Rb;
 #pragma unroll
       for (int k = 0; k < 9; ++k) Rb.m[k] = 0.f;
-      for (int k = __ldg(M.li_ptr + i); k < __ldg(M.li_ptr + i + 1); ++k) {
-        const int e = __ldg(M.li_idx + k);
-        if (e < M.nc) continue;
-        const V3 xb = ld3(w, M.o_ITB + 10 * e);
-        Pb = Pb + xb;
-        add_outer(Rb, xb, cld3(M.item_pos + 3 * e));
-      }
-      add3(w, M.o_PB + 3 * i, Pb);
+      for (int r = 0; r < parts; ++r) {
+        const int o = M.o_MW + 12 * (i * parts + r);
+        Pb = Pb + ld3(w, o);
 #pragma unroll
-      for (int k = 0; k < 9; ++k) w[M.o_RB + 9 * i + k] += Rb.m[k];
+        for (int k = 0; k < 9; ++k) Rb.m[k] += w[o + 3 + k];
+      }
+      add3(w, lwork(M, i) + LW_PB, Pb);
+#pragma unroll
+      for (int k = 0; k < 9; ++k) w[lwork(M, i) + LW_RB + k] += Rb.m[k];
     }
     team_sync(nl);
   }
@@ -1465,6 +1519,10 @@ __device__ __forceinline__ void st_dynamics_adj(const DevModel& M, const Mem& w,
         if (i == hd) break;
       }
     }
+    team_sync(nl);
+  }
+  if (M.root_free) {
+    for (int d = lane; d < 6; d += nl) root_dof_terms(M, w, d);
     team_sync(nl);
   }
   for (int i = lane; i < M.L; i += nl) lk_adj_qbar(M, w, i);

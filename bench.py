@@ -83,10 +83,13 @@ def algo_bytes_per_env_step(model):
 
 
 # DRAM traffic (read + write) per launch of the batched kernels on the full
-# ant-2048 h = 32 window, from one-pass ncu captures (dram__bytes_read.sum +
-# dram__bytes_write.sum of one launch); None where no capture of the current
-# kernels exists.
-TRAFFIC_BYTES_PER_LAUNCH = {"ant-2048": {"forward": None, "adjoint_recompute": None, "adjoint_tape": None}}
+# ant-2048 h = 32 window, from a one-pass ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum of one launch of each kernel); None where no capture of
+# the current kernels exists.  The recomputing adjoint's traffic is mostly its
+# per-step substep records (about 91 MB per step for 2048 environments)
+# written back from L2 as they are replaced step after step.
+TRAFFIC_BYTES_PER_LAUNCH = {"ant-2048": {"forward": 2.451968e6 + 0.0, "adjoint_recompute": 198.692608e6 + 2438.920704e6,
+                                         "adjoint_tape": None}}
 
 
 def fp32_peak_tflops(n_sms: int, sm_mhz: float) -> float:
@@ -747,6 +750,16 @@ def oracle_single_core_rate(workload: str):
         return None
 
 
+# Gradient validity gate per sampled environment: relative error <= 1e-3, or
+# <= GRAD_FLOOR_FACTOR x the environment's FP32 floor (environments whose own
+# gradient moves by more than 1e-4 when the oracle's operations are rounded at
+# FP32's unit roundoff: a contact, friction or limit switch within rounding of
+# its threshold somewhere in the window).
+GRAD_RTOL = 1e-3
+GRAD_FLOOR_RUNS = 3
+GRAD_FLOOR_FACTOR = 10.0
+
+
 def gradient_check(sim, groups, outf, outa, act, rbar, n_sample: int = 4):
     """Per group: the maximum over sampled environments of the per-environment
     relative error (2-norm) of the window gradients (action and initial-state
@@ -771,15 +784,18 @@ def gradient_check(sim, groups, outf, outa, act, rbar, n_sample: int = 4):
         ref = np.concatenate([ab.transpose(1, 0, 2).reshape(len(envs), -1), qb, qdb], axis=1)
         rel = np.linalg.norm(got - ref, axis=1) / np.linalg.norm(ref, axis=1)
         # FP32 floor of each environment's gradient along the same checkpoints:
-        # the oracle's own deviation with every operation perturbed at FP32's
-        # unit roundoff (Monte Carlo Arithmetic, one run)
-        mc = o.mca_window_adjoint(qt.transpose(0, 2, 1), qdt.transpose(0, 2, 1), a.transpose(0, 2, 1), rb,
-                                  np.zeros((len(envs), model.nq)), np.zeros((len(envs), model.nv)), seed=11,
-                                  tangents=False)
-        mref = np.concatenate([mc[2].transpose(1, 0, 2).reshape(len(envs), -1), mc[0], mc[1]], axis=1)
-        floor = np.linalg.norm(mref - ref, axis=1) / np.linalg.norm(ref, axis=1)
+        # the oracle's own largest deviation over GRAD_FLOOR_RUNS runs with every
+        # operation perturbed at FP32's unit roundoff (Monte Carlo Arithmetic)
+        floor = np.zeros(len(envs))
+        for k in range(GRAD_FLOOR_RUNS):
+            mc = o.mca_window_adjoint(qt.transpose(0, 2, 1), qdt.transpose(0, 2, 1), a.transpose(0, 2, 1), rb,
+                                      np.zeros((len(envs), model.nq)), np.zeros((len(envs), model.nv)),
+                                      seed=11 + k, tangents=False)
+            mref = np.concatenate([mc[2].transpose(1, 0, 2).reshape(len(envs), -1), mc[0], mc[1]], axis=1)
+            floor = np.maximum(floor, np.linalg.norm(mref - ref, axis=1) / np.linalg.norm(ref, axis=1))
+        ok = rel <= np.maximum(GRAD_RTOL, GRAD_FLOOR_FACTOR * floor)
         out[f"{gi}:{model.name}"] = {"max": float(rel.max()), "envs": envs.tolist(), "rel": rel.tolist(),
-                                     "fp32_floor": floor.tolist()}
+                                     "fp32_floor": floor.tolist(), "within_gate": bool(ok.all())}
         off += N
     return out
 

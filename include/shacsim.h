@@ -312,6 +312,26 @@ shac_status shac_autotune(shac_batch* batch, void* stream, void* workspace, int3
  * the timed windows' buffers). */
 size_t shac_autotune_workspace_bytes(const shac_batch* batch);
 
+/* Model-specialised batched kernels.  The paper generates its simulation
+ * kernels from source per task (Sec. 3.1, source-code transformation); here
+ * the library's own batched kernels are compiled again at run time with one
+ * model's counts and scratch offsets and the current team size written into
+ * their source as constants, so that the compiler folds the address
+ * arithmetic and the loop bounds they control.  enable = 1 builds the forward
+ * and adjoint kernels for the batch's model and current launch shape with
+ * NVRTC on the current device (which must be the batch's; a few seconds, once
+ * per distinct model layout and team size in a process) and makes every
+ * batched step and window call of the batch use them while group 0 keeps that
+ * team size (after shac_batch_set_launch or shac_autotune change it, the calls
+ * use the generic kernels again until the next shac_batch_specialize);
+ * enable = 0 returns to the generic kernels.  Results equal the generic
+ * kernels' up to FP32 rounding (constant operands can change how the compiler
+ * contracts multiply-adds).  BATCHED batches with one group only
+ * (SHAC_ERR_UNSUPPORTED otherwise).  Synchronous; not for a stream capture.
+ * Errors: SHAC_ERR_INVALID_ARG (null batch, enable not 0/1, another device
+ * current); SHAC_ERR_CUDA if the run-time compiler or the module load fails. */
+shac_status shac_batch_specialize(shac_batch* batch, int32_t enable);
+
 /* Window tape (BATCHED form; SHAC_ERR_UNSUPPORTED for PLAIN): keep = 1 makes
  * shac_window_forward (and its episodic variant) store every substep record of
  * every step (link poses, inertias, subspaces, velocities, external wrenches,

@@ -28,6 +28,7 @@ EXPORTED = [
     "shac_window_adjoint", "shac_window_forward_episodic", "shac_window_adjoint_episodic", "shac_batch_set_launch",
     "shac_batch_get_launch", "shac_batch_set_window_tape", "shac_get_status", "shac_status_string",
     "shac_step_adjoint_static", "shac_td_lambda", "shac_autotune", "shac_autotune_workspace_bytes",
+    "shac_batch_specialize",
 ]
 
 
@@ -106,6 +107,8 @@ def load(path: str = LIB_PATH):
     L.shac_batch_set_window_tape.restype = ctypes.c_int
     L.shac_autotune.argtypes = [_vp, _vp, _vp, ctypes.c_int32]
     L.shac_autotune.restype = ctypes.c_int
+    L.shac_batch_specialize.argtypes = [_vp, ctypes.c_int32]
+    L.shac_batch_specialize.restype = ctypes.c_int
     L.shac_autotune_workspace_bytes.argtypes = [_vp]
     L.shac_autotune_workspace_bytes.restype = ctypes.c_size_t
     L.shac_batch_get_launch.argtypes = [_vp, ctypes.c_int32, _i32p, _i32p]

@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "../../include/shacsim.h"
+#include "shac_jit.h"
 #include "shac_kernels.cuh"
 
 using namespace shac;
@@ -53,6 +54,10 @@ struct shac_batch {
   size_t ws_step = 0;                    // bytes the step-level calls use (a prefix of the workspace)
   std::vector<size_t> window_tape_off;   // bytes
   std::vector<int64_t> window_tape_step; // floats per step per environment slot
+  // model-specialised kernels (shac_batch_specialize): used while group 0 keeps
+  // the team size they were built for
+  JitKernels spec;
+  int spec_lanes = 0;
 };
 
 static shac_status cuda_ok(cudaError_t e) { return e == cudaSuccess ? SHAC_OK : SHAC_ERR_CUDA; }
@@ -535,6 +540,27 @@ extern "C" shac_status shac_batch_set_window_tape(shac_batch* b, int32_t keep) {
   return SHAC_OK;
 }
 
+extern "C" shac_status shac_batch_specialize(shac_batch* b, int32_t enable) {
+  if (!b || (enable != 0 && enable != 1)) return SHAC_ERR_INVALID_ARG;
+  if (!enable) {
+    b->spec = JitKernels{};
+    b->spec_lanes = 0;
+    return SHAC_OK;
+  }
+  if (b->form != SHAC_FORM_BATCHED || b->groups.size() != 1) return SHAC_ERR_UNSUPPORTED;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return SHAC_ERR_CUDA;
+  if (dev != b->device) return SHAC_ERR_INVALID_ARG;
+  const Group& g = b->groups[0];
+  JitKernels k;
+  const shac_status st = jit_kernels(b->device, g.m->layout, g.lanes, dense_class(g.m->nv, g.lanes),
+                                     env_stride(g.m, g.lanes), &k, nullptr);
+  if (st != SHAC_OK) return st;
+  b->spec = k;
+  b->spec_lanes = g.lanes;
+  return SHAC_OK;
+}
+
 extern "C" shac_status shac_batch_get_launch(const shac_batch* b, int32_t group, int32_t* lanes, int32_t* warps) {
   if (!b || group < 0 || group >= (int)b->groups.size()) return SHAC_ERR_INVALID_ARG;
   if (lanes) *lanes = b->groups[group].lanes;
@@ -583,14 +609,30 @@ static shac_status batched_launch(shac_batch* b, BatchedArgs& a, void* ws, cudaS
   if (W < 1) return SHAC_ERR_CAPACITY;
   const size_t smem = (size_t)W * a.smem_warp_floats * sizeof(float);
   const int block = 32 * W;
+  // the model-specialised kernels while the launch shape is the one they were built for
+  const void* spec = nullptr;
+  if (b->spec.key != 0u && b->spec_lanes == b->groups[0].lanes) {
+    spec = adjoint ? b->spec.adj : b->spec.fwd;
+    a.spec_key = b->spec.key;
+  }
   // Static plus dynamic shared memory above 48 KB needs the opt-in attribute;
   // the kernels' static part (the model table) is under 8 KB.
-  if (smem > 40 * 1024 && batched_set_smem_limit(smem) != cudaSuccess) return SHAC_ERR_CAPACITY;
+  if (smem > 40 * 1024) {
+    const cudaError_t e = spec ? cudaFuncSetAttribute(spec, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                               : batched_set_smem_limit(smem);
+    if (e != cudaSuccess) return SHAC_ERR_CAPACITY;
+  }
   int occ = 0;
-  if (batched_occupancy(&occ, block, smem, adjoint) != cudaSuccess) return SHAC_ERR_CUDA;
+  const cudaError_t oe = spec ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, spec, block, smem)
+                              : batched_occupancy(&occ, block, smem, adjoint);
+  if (oe != cudaSuccess) return SHAC_ERR_CUDA;
   if (occ < 1) return SHAC_ERR_CAPACITY;
   const int grid = std::max(1, std::min(b->num_sms * occ, (b->n_items + W - 1) / W));
   if (cudaMemsetAsync(a.counter, 0, sizeof(int), s) != cudaSuccess) return SHAC_ERR_CUDA;
+  if (spec) {
+    void* args[] = {&a};
+    return cuda_ok(cudaLaunchKernel(spec, dim3(grid), dim3(block), args, smem, s));
+  }
   if (adjoint) launch_batched_adjoint(a, grid, block, smem, s);
   else launch_batched_forward(a, grid, block, smem, s);
   return cuda_ok(cudaGetLastError());

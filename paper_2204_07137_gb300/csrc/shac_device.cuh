@@ -34,14 +34,29 @@
 // that a team performs in a different order (there is none: every
 // reduction below is a fixed-order gather).
 #pragma once
-#include <utility>
+#ifndef __CUDACC_RTC__
 #include <cuda_runtime.h>
 #include <stdint.h>
+#else
+// compiled at run time (a model-specialised build of the batched kernels):
+// no host headers
+typedef long long int64_t;
+typedef unsigned long long uint64_t;
+typedef int int32_t;
+typedef unsigned int uint32_t;
+#endif
 
 namespace shac {
 
+// Compile-time integer sequences (the dense path expands its column loops
+// through them).
+template <int... I> struct iseq {};
+template <int N, int... I> struct make_iseq_t : make_iseq_t<N - 1, N - 1, I...> {};
+template <int... I> struct make_iseq_t<0, I...> { using type = iseq<I...>; };
+template <int N> using make_iseq = typename make_iseq_t<N>::type;
+
 enum { J_FREE = 0, J_REV = 1, J_PRIS = 2, J_FIXED = 3 };
-enum { FLAG_NONFINITE = 1u };
+enum { FLAG_NONFINITE = 1u, FLAG_SPEC_MISMATCH = 2u };
 
 constexpr int MAX_LINKS = 64;
 constexpr int MAX_DOF = 32;
@@ -743,7 +758,7 @@ __device__ __forceinline__ void chol_update(float (&row)[NM], float lik, int lan
 }
 template <int K, int NM, int... J>
 __device__ __forceinline__ void chol_trailing(float (&row)[NM], float lik, int lane, int nl,
-                                              std::integer_sequence<int, J...>) {
+                                              iseq<J...>) {
   (chol_update<K + 1 + J, NM>(row, lik, lane, nl), ...);
 }
 // Column K: L_KK = sqrt(pivot) (lane K), L_iK = M_iK / L_KK (lanes i > K).
@@ -754,11 +769,11 @@ __device__ __forceinline__ void chol_column(float (&row)[NM], float& inv_diag, i
   const float lik = rk * inv;
   if (lane >= K) row[K] = lik;
   if (lane == K) inv_diag = inv;
-  chol_trailing<K, NM>(row, lik, lane, nl, std::make_integer_sequence<int, NM - K - 1>{});
+  chol_trailing<K, NM>(row, lik, lane, nl, make_iseq<NM - K - 1>{});
 }
 template <int NM, int... K>
 __device__ __forceinline__ void chol_columns(float (&row)[NM], float& inv_diag, int lane, int nl,
-                                             std::integer_sequence<int, K...>) {
+                                             iseq<K...>) {
   (chol_column<K, NM>(row, inv_diag, lane, nl), ...);
 }
 
@@ -772,7 +787,7 @@ __device__ __forceinline__ void fsub_step(const float (&row)[NM], float inv_diag
 }
 template <int NM, int... K>
 __device__ __forceinline__ void fsub(const float (&row)[NM], float inv_diag, float& b, int lane, int nl,
-                                     std::integer_sequence<int, K...>) {
+                                     iseq<K...>) {
   (fsub_step<K, NM>(row, inv_diag, b, lane, nl), ...);
 }
 // Backward substitution x = L^{-T} y, step K (descending): lane a < K needs
@@ -790,7 +805,7 @@ __device__ __forceinline__ void bsub_step(const DevModel& M, const Mem& w, float
 }
 template <int NM, class Mem, int... K>
 __device__ __forceinline__ void bsub(const DevModel& M, const Mem& w, float inv_diag, float& b, int lane, int nl,
-                                     std::integer_sequence<int, K...>) {
+                                     iseq<K...>) {
   (bsub_step<NM - 1 - K>(M, w, inv_diag, b, lane, nl), ...);
 }
 
@@ -807,7 +822,7 @@ __device__ __forceinline__ void row_entry(const DevModel& M, const Mem& w, float
 }
 template <int NM, class Mem, int... B>
 __device__ __forceinline__ void row_assemble(const DevModel& M, const Mem& w, float (&row)[NM], int lane,
-                                             std::integer_sequence<int, B...>) {
+                                             iseq<B...>) {
   V3 fn = v3(0.f, 0.f, 0.f), ff = v3(0.f, 0.f, 0.f);
   unsigned mask = 0u;
   const bool own = lane < M.nv;
@@ -825,7 +840,7 @@ __device__ __forceinline__ void row_store_entry(const DevModel& M, const Mem& w,
 }
 template <int NM, class Mem, int... B>
 __device__ __forceinline__ void row_store(const DevModel& M, const Mem& w, const float (&row)[NM], int lane,
-                                          std::integer_sequence<int, B...>) {
+                                          iseq<B...>) {
   (row_store_entry<B, NM>(M, w, row, lane), ...);
 }
 template <int B, int NM, class Mem>
@@ -836,7 +851,7 @@ __device__ __forceinline__ void row_load_entry(const DevModel& M, const Mem& w, 
 }
 template <int NM, class Mem, int... B>
 __device__ __forceinline__ void row_load(const DevModel& M, const Mem& w, float (&row)[NM], int lane,
-                                         std::integer_sequence<int, B...>) {
+                                         iseq<B...>) {
   (row_load_entry<B, NM>(M, w, row, lane), ...);
 }
 
@@ -844,7 +859,7 @@ __device__ __forceinline__ void row_load(const DevModel& M, const Mem& w, float 
 // (M + diag(arm)) qdd = b into o_QDD.  b is lane a's right-hand side.
 template <int NM, class Mem>
 __device__ __forceinline__ void dense_substep(const DevModel& M, const Mem& w, int lane, int nl, float b) {
-  using Seq = std::make_integer_sequence<int, NM>;
+  using Seq = make_iseq<NM>;
   const bool own = lane < M.nv;
   float row[NM];
   row_assemble<NM>(M, w, row, lane, Seq{});
@@ -865,7 +880,7 @@ __device__ __forceinline__ void dense_substep(const DevModel& M, const Mem& w, i
 template <int NM, class Mem>
 __device__ __forceinline__ void dense_stored_solve(const DevModel& M, const Mem& w, int lane, int nl, int o_in,
                                                    int o_out) {
-  using Seq = std::make_integer_sequence<int, NM>;
+  using Seq = make_iseq<NM>;
   const bool own = lane < M.nv;
   float row[NM];
   row_load<NM>(M, w, row, lane, Seq{});

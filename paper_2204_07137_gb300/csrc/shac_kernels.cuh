@@ -72,8 +72,13 @@ struct BatchedArgs {
   int* ep_step;             // [n_envs] steps since the last reset (in/out)
   unsigned char* done;      // forward: [h][n_envs] episode ended by step t
   const unsigned char* done_in;   // adjoint: the forward's done mask
+  // key of the model-specialised kernels these arguments are for (0: the
+  // generic kernels); a specialised kernel given another key does nothing but
+  // raise FLAG_SPEC_MISMATCH
+  unsigned int spec_key;
 };
 
+#ifndef __CUDACC_RTC__
 void launch_batched_forward(const BatchedArgs& a, int grid, int block, size_t smem, cudaStream_t s);
 void launch_batched_adjoint(const BatchedArgs& a, int grid, int block, size_t smem, cudaStream_t s);
 cudaError_t batched_occupancy(int* blocks_per_sm, int block, size_t smem, bool adjoint);
@@ -111,5 +116,6 @@ void launch_plain_adj_store_act(const PlainGroup& g, float* act_bar, int64_t act
 // writes (QB + qb_add, QDB + qdb_add) (adds skipped when null)
 void launch_plain_adj_store_state(const PlainGroup& g, float* qb, float* qdb, const float* qb_add,
                                   const float* qdb_add, int64_t q_off, int64_t qd_off, cudaStream_t s);
+#endif
 
 }  // namespace shac

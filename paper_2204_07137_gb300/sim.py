@@ -90,6 +90,13 @@ class Simulator:
         self._alloc_workspace()
         return [self.get_launch(g) for g in range(len(self.groups))]
 
+    def specialize(self, enable: bool = True):
+        """Use (or stop using) batched kernels compiled at run time for this
+        batch's model and current team size (shac_batch_specialize): a few
+        seconds the first time per model layout and team size in a process.
+        Single-group batched simulators only."""
+        _lib.check(_lib.load().shac_batch_specialize(self.batch, int(bool(enable))), "shac_batch_specialize")
+
     def get_launch(self, group: int) -> Tuple[int, int]:
         l, w = ctypes.c_int32(), ctypes.c_int32()
         _lib.check(_lib.load().shac_batch_get_launch(self.batch, group, ctypes.byref(l), ctypes.byref(w)),

@@ -1,5 +1,6 @@
 """Full-size workloads in the launch configuration the bench times (batched
-form, launch shape chosen by the library's autotuner, per-step checkpoints,
+form, launch shape chosen by the library's autotuner, kernels compiled for the
+model and that shape when the batch has one group, per-step checkpoints,
 substeps recomputed in the adjoint), h = 32: sampled environments of every
 articulation group checked against the FP64 oracle -
 
@@ -44,6 +45,8 @@ def test_full_size_window_matches_oracle(oracle_mod, workload, n_sample):
     wl = I.workload(workload)
     sim = Simulator(wl.groups, form="batched", h_max=H)
     sim.autotune_native(budget_ms=3000)
+    if len(wl.groups) == 1:
+        sim.specialize()
     q0 = sim.pack([I.initial_state(m, n, 0)[0] for m, n in wl.groups], "q")
     qd0 = sim.pack([I.initial_state(m, n, 0)[1] for m, n in wl.groups], "qd")
     act = torch.cat([torch.from_numpy(I.window_actions(m, n, H, 0).reshape(H, -1)) for m, n in wl.groups],

@@ -82,13 +82,14 @@ def algo_bytes_per_env_step(model):
     return {"forward": 4 * (2 * s + model.na + 1), "adjoint": 4 * (3 * s + 2 * model.na + 1)}
 
 
-# DRAM traffic (read + write) per launch of the batched kernels on the full
-# ant-2048 h = 32 window, from a one-pass ncu capture (dram__bytes_read.sum +
-# dram__bytes_write.sum of one launch of each kernel); None where no capture of
-# the current kernels exists.  The recomputing adjoint's traffic is mostly its
-# per-step substep records (about 91 MB per step for 2048 environments)
-# written back from L2 as they are replaced step after step.
-TRAFFIC_BYTES_PER_LAUNCH = {"ant-2048": {"forward": 2.451968e6 + 0.0, "adjoint_recompute": 198.692608e6 + 2438.920704e6,
+# DRAM traffic (read + write) per launch of the model-specialised batched
+# kernels on the full ant-2048 h = 32 window, from a one-pass ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum of one launch of each kernel);
+# None where no capture of the current kernels exists.  The recomputing
+# adjoint's traffic is mostly its per-step substep records (about 91 MB per
+# step for 2048 environments) written back from L2 as they are replaced step
+# after step.
+TRAFFIC_BYTES_PER_LAUNCH = {"ant-2048": {"forward": 2.409472e6 + 0.0, "adjoint_recompute": 200.035072e6 + 2406.965504e6,
                                          "adjoint_tape": None}}
 
 
@@ -114,7 +115,7 @@ def parse():
     p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     p.add_argument("--plain-steps", type=int, default=20)
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--workload", default=WORKLOAD)
+    p.add_argument("--workload", default=None, help=f"workload name (default {WORKLOAD}; mtu-512 with --policy)")
     p.add_argument("--grad-check-envs", type=int, default=4,
                    help="sampled environments of every group checked against the oracle (0: skip)")
     p.add_argument("--autotune-ms", type=int, default=5000,
@@ -145,7 +146,10 @@ def parse():
                    help="config 5 with the policy MLP in the loop (workload mtu-512): graph-captured window of "
                         "policy + library steps + autograd through the step adjoints, timed beside the step loop "
                         "without the network and the open-loop window")
-    return p.parse_args()
+    args = p.parse_args()
+    if args.workload is None:
+        args.workload = "mtu-512" if args.policy else WORKLOAD
+    return args
 
 
 # ------------------------------------------------------------------ clocks --
@@ -520,7 +524,12 @@ def gpu_main(args, rank, world, dist):
                 "chosen": {"lanes_per_env": [l for l, _ in shape], "warps_per_cta": shape[0][1]},
                 "search": "coordinate descent over lanes per environment (each group) then warps per CTA, "
                           f"h = 8 windows from the rest configuration (median of 3; a change needs a 3 % gain), budget "
-                          f"{args.autotune_ms} ms"}
+                          f"{args.autotune_ms} ms",
+                "note": "ms_per_window of each shape: graph replay of the h = 32 window with the generic kernels "
+                        "(before any specialisation), median of 5"}
+        g1, _, _ = capture_window(sim, q0, qd0, act, rbar, zq, zqd, stream)
+        tune["chosen"]["ms_per_window"] = timed(g1.replay, 5, 2)
+        del g1
     shape = [sim.get_launch(g) for g in range(len(groups))]
     # kernels compiled for this model and launch shape (single-group batches)
     spec_s = None
@@ -536,9 +545,6 @@ def gpu_main(args, rank, world, dist):
         sampler.start()
     ms_window = timed(graph.replay, args.steps, args.warmup)
     clocks = sampler.stop() if sampler else None
-    if tune is not None:
-        tune["chosen"]["ms_per_window"] = timed(graph.replay, 5, 1)
-        tune["default"]["note"] = "ms_per_window of each shape: graph replay of the h = 32 window, median of 5"
 
     # per-kernel durations (eager launches, same stream) for the roofline
     def one_fwd():
@@ -663,6 +669,8 @@ def gpu_main(args, rank, world, dist):
     achieved = None if dom_flops is None else dom_flops * per_launch / (ms_dom * 1e-3) / 1e12
     traffic = TRAFFIC_BYTES_PER_LAUNCH.get(wl.name, {}).get("adjoint_recompute" if dominant == "adjoint"
                                                              else "forward")
+    if spec_s is None:   # the capture is of the specialised kernels
+        traffic = None
     hbm_peak, hbm_src = measured_hbm_gbs()
     dom_bytes = None if bytes_alg is None else bytes_alg[dominant] * per_launch
     # the window's work (forward + recompute + reverse) over each form's window time
@@ -834,6 +842,9 @@ def policy_main(args, rank, world, dist):
     model, N = wl.groups[0]
     seed = shard_seed(rank)
     sim = Simulator(wl.groups, form="batched", h_max=1)
+    if args.autotune_ms > 0:   # the library's launch-shape search, as for the contract line
+        sim.autotune_native(budget_ms=args.autotune_ms)
+    shape = sim.get_launch(0)
     if not args.no_specialize:
         sim.specialize()
     g = torch.Generator().manual_seed(seed)
@@ -870,6 +881,7 @@ def policy_main(args, rank, world, dist):
     g_pol, out_pol = capture(with_policy)
     g_act, out_act = capture(without_policy)
     wsim = Simulator(wl.groups, form="batched", h_max=H)
+    wsim.set_launch(0, shape[0], shape[1])
     if not args.no_specialize:
         wsim.specialize()
     rbar = torch.full((H, N), 1.0 / (N * H), device=dev)
@@ -900,6 +912,8 @@ def policy_main(args, rank, world, dist):
                                                        f"sigmoid; {n_params} parameters, weights ~ N(0, 0.05)",
                    "form": "per step: observation, MLP, library step (shac_step); backward: autograd through "
                            "the library's step adjoint (substeps recomputed) into the MLP; one CUDA graph",
+                   "lanes_per_env": shape[0], "warps_per_cta": shape[1],
+                   "kernels": "generic" if args.no_specialize else "model-specialised",
                    "timing": "median of the timed steps", "l2": "flushed (256 MB write) before each timed step"},
         "without_policy": {"value": env_steps / (ms_act * 1e-3), "unit": "env-steps/s", "ms_per_step": ms_act,
                            "form": "the same step loop with given actions, gradient w.r.t. the actions"},

@@ -518,25 +518,32 @@ def gpu_main(args, rank, world, dist):
         g0, _, _ = capture_window(sim, q0, qd0, act, rbar, zq, zqd, stream)
         ms_default = timed(g0.replay, 5, 2)
         del g0
-        shape = sim.autotune_native(budget_ms=args.autotune_ms, stream=stream)
+        shape = sim.autotune_native(budget_ms=args.autotune_ms, stream=stream, q0=q0, qd0=qd0, act=act)
         tune = {"default": {"lanes_per_env": [l for l, _ in default_shape], "warps_per_cta": default_shape[0][1],
                             "ms_per_window": ms_default},
                 "chosen": {"lanes_per_env": [l for l, _ in shape], "warps_per_cta": shape[0][1]},
                 "search": "coordinate descent over lanes per environment (each group) then warps per CTA, "
-                          f"h = 8 windows from the rest configuration (median of 3; a change needs a 3 % gain), budget "
+                          f"h = 8 windows of the workload's inputs (median of 3; a change needs a 3 % gain), budget "
                           f"{args.autotune_ms} ms",
                 "note": "ms_per_window of each shape: graph replay of the h = 32 window with the generic kernels "
                         "(before any specialisation), median of 5"}
         g1, _, _ = capture_window(sim, q0, qd0, act, rbar, zq, zqd, stream)
         tune["chosen"]["ms_per_window"] = timed(g1.replay, 5, 2)
         del g1
-    shape = [sim.get_launch(g) for g in range(len(groups))]
-    # kernels compiled for this model and launch shape (single-group batches)
+    # kernels compiled for this model and launch shape (single-group batches);
+    # the search then re-times the warps per CTA with them (it keeps the team
+    # size they were compiled for)
     spec_s = None
     if len(groups) == 1 and not args.no_specialize:
         t0 = time.perf_counter()
         sim.specialize()
         spec_s = time.perf_counter() - t0
+        if tune is not None:
+            w_gen = sim.get_launch(0)[1]
+            sim.autotune_native(budget_ms=args.autotune_ms, stream=stream, q0=q0, qd0=qd0, act=act)
+            tune["specialised"] = {"warps_per_cta": sim.get_launch(0)[1], "generic_choice": w_gen,
+                                   "search": "warps per CTA with the specialised kernels, same rule"}
+    shape = [sim.get_launch(g) for g in range(len(groups))]
 
     # ---- the configured variant: graph-captured forward + recomputing adjoint
     graph, outf, outa = capture_window(sim, q0, qd0, act, rbar, zq, zqd, stream)
@@ -842,17 +849,20 @@ def policy_main(args, rank, world, dist):
     model, N = wl.groups[0]
     seed = shard_seed(rank)
     sim = Simulator(wl.groups, form="batched", h_max=1)
-    if args.autotune_ms > 0:   # the library's launch-shape search, as for the contract line
-        sim.autotune_native(budget_ms=args.autotune_ms)
-    shape = sim.get_launch(0)
-    if not args.no_specialize:
-        sim.specialize()
     g = torch.Generator().manual_seed(seed)
     pol = PolicyMLP(observation_size(model), model.na, generator=g).to(dev)
     params = list(pol.parameters())
     q0 = sim.pack([I.initial_state(model, N, seed)[0]], "q")
     qd0 = sim.pack([I.initial_state(model, N, seed)[1]], "qd")
     acts = torch.from_numpy(I.window_actions(model, N, H, seed).reshape(H, -1)).to(dev).contiguous()
+    # the library's launch-shape search on this workload, as for the contract line
+    if args.autotune_ms > 0:
+        sim.autotune_native(budget_ms=args.autotune_ms, q0=q0, qd0=qd0, act=acts)
+    if not args.no_specialize:
+        sim.specialize()
+        if args.autotune_ms > 0:
+            sim.autotune_native(budget_ms=args.autotune_ms, q0=q0, qd0=qd0, act=acts)
+    shape = sim.get_launch(0)
     acts.requires_grad_(True)
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.Stream(device=dev)

@@ -293,11 +293,17 @@ shac_status shac_batch_get_launch(const shac_batch* batch, int32_t group, int32_
  * lanes per environment in turn (1, 2, 4, 8, 16, 32; the others fixed), then
  * the warps per CTA (1, 2, 4, 8); every candidate is timed as a window forward
  * + window adjoint of min(h_max, 8) steps with CUDA events on `stream` (one
- * warm-up, median of three), from the rest configuration (joint coordinates 0,
- * free joints at the origin with the identity orientation, zero velocities and
- * actions).  A candidate replaces the best shape so far only when it is more
+ * warm-up, median of three).  The timed windows start from q0 [q_size] and
+ * qd0 [qd_size] and apply act [min(h_max, 8)][act_size] (device pointers, the
+ * layouts of the window calls; read once at the start), so the search sees the
+ * caller's workload (its contacts and joint ranges); a null pointer takes the
+ * rest configuration instead (joint coordinates 0, free joints at the origin
+ * with the identity orientation, zero velocities, zero actions).  A candidate replaces the best shape so far only when it is more
  * than 3 % faster (timing noise between equal shapes stays below that); the
- * best shape is applied to the batch (as shac_batch_set_launch would) and kept.  `workspace`: a caller buffer of
+ * best shape is applied to the batch (as shac_batch_set_launch would) and
+ * kept.  A batch using model-specialised kernels (shac_batch_specialize) keeps
+ * its team size and searches the warps per CTA only, timed with those
+ * kernels (they stay in use).  `workspace`: a caller buffer of
  * shac_autotune_workspace_bytes (256-byte aligned), overwritten: the batch's
  * workspace followed by the inputs and outputs of the timed windows; the call
  * allocates no device memory.  budget_ms: wall-clock limit of the search
@@ -307,20 +313,22 @@ shac_status shac_batch_get_launch(const shac_batch* batch, int32_t group, int32_
  * SHAC_ERR_INVALID_ARG for a null batch, an unaligned workspace or
  * budget_ms <= 0; SHAC_ERR_CUDA if a CUDA call fails (the launch shape is then
  * left as it was). */
-shac_status shac_autotune(shac_batch* batch, void* stream, void* workspace, int32_t budget_ms);
+shac_status shac_autotune(shac_batch* batch, void* stream, void* workspace, int32_t budget_ms, const float* q0,
+                          const float* qd0, const float* act);
 /* Bytes of the workspace shac_autotune needs (shac_batch_workspace_bytes plus
  * the timed windows' buffers). */
 size_t shac_autotune_workspace_bytes(const shac_batch* batch);
 
-/* Model-specialised batched kernels.  The paper generates its simulation
- * kernels from source per task (Sec. 3.1, source-code transformation); here
- * the library's own batched kernels are compiled again at run time with one
- * model's counts and scratch offsets and the current team size written into
- * their source as constants, so that the compiler folds the address
- * arithmetic and the loop bounds they control.  enable = 1 builds the forward
+/* Model-specialised batched kernels.  The paper generates its forward and
+ * backward simulation kernels by source-code transformation (Sec. 3.1); here
+ * run-time compilation serves another end: the library's own batched kernels
+ * are compiled again with one model's counts, scratch offsets and link parents
+ * and the current team size written into their source as constants, so that
+ * the compiler folds the address arithmetic and the loop bounds they control
+ * and unrolls the tree sums over the links.  enable = 1 builds the forward
  * and adjoint kernels for the batch's model and current launch shape with
  * NVRTC on the current device (which must be the batch's; a few seconds, once
- * per distinct model layout and team size in a process) and makes every
+ * per distinct model layout, tree and team size in a process) and makes every
  * batched step and window call of the batch use them while group 0 keeps that
  * team size (after shac_batch_set_launch or shac_autotune change it, the calls
  * use the generic kernels again until the next shac_batch_specialize);

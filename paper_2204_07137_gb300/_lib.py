@@ -105,7 +105,7 @@ def load(path: str = LIB_PATH):
     L.shac_td_lambda.restype = ctypes.c_int
     L.shac_batch_set_window_tape.argtypes = [_vp, ctypes.c_int32]
     L.shac_batch_set_window_tape.restype = ctypes.c_int
-    L.shac_autotune.argtypes = [_vp, _vp, _vp, ctypes.c_int32]
+    L.shac_autotune.argtypes = [_vp, _vp, _vp, ctypes.c_int32, _vp, _vp, _vp]
     L.shac_autotune.restype = ctypes.c_int
     L.shac_batch_specialize.argtypes = [_vp, ctypes.c_int32]
     L.shac_batch_specialize.restype = ctypes.c_int

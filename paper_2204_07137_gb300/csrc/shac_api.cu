@@ -553,7 +553,7 @@ extern "C" shac_status shac_batch_specialize(shac_batch* b, int32_t enable) {
   if (dev != b->device) return SHAC_ERR_INVALID_ARG;
   const Group& g = b->groups[0];
   JitKernels k;
-  const shac_status st = jit_kernels(b->device, g.m->layout, g.lanes, dense_class(g.m->nv, g.lanes),
+  const shac_status st = jit_kernels(b->device, g.m->layout, g.m->parent, g.lanes, dense_class(g.m->nv, g.lanes),
                                      env_stride(g.m, g.lanes), &k, nullptr);
   if (st != SHAC_OK) return st;
   b->spec = k;
@@ -919,7 +919,8 @@ extern "C" size_t shac_autotune_workspace_bytes(const shac_batch* b) {
   return b->ws_total + autotune_parts(b, parts);
 }
 
-extern "C" shac_status shac_autotune(shac_batch* b, void* stream, void* ws, int32_t budget_ms) {
+extern "C" shac_status shac_autotune(shac_batch* b, void* stream, void* ws, int32_t budget_ms, const float* q0_in,
+                                     const float* qd0_in, const float* act_in) {
   if (!b || !aligned_ws(b, ws) || budget_ms <= 0) return SHAC_ERR_INVALID_ARG;
   if (b->form != SHAC_FORM_BATCHED || b->n_items == 0) return SHAC_OK;
   const auto t0 = std::chrono::steady_clock::now();
@@ -952,6 +953,13 @@ extern "C" shac_status shac_autotune(shac_batch* b, void* stream, void* ws, int3
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   shac_status st = cuda_ok(cudaMemsetAsync(buf, 0, buf_bytes, s));
   if (st == SHAC_OK) st = cuda_ok(cudaMemcpyAsync(q0, qh.data(), nq * sizeof(float), cudaMemcpyHostToDevice, s));
+  // the caller's window inputs replace the rest configuration where given
+  if (st == SHAC_OK && q0_in)
+    st = cuda_ok(cudaMemcpyAsync(q0, q0_in, nq * sizeof(float), cudaMemcpyDeviceToDevice, s));
+  if (st == SHAC_OK && qd0_in)
+    st = cuda_ok(cudaMemcpyAsync(qd0, qd0_in, nqd * sizeof(float), cudaMemcpyDeviceToDevice, s));
+  if (st == SHAC_OK && act_in)
+    st = cuda_ok(cudaMemcpyAsync(act, act_in, (size_t)h * b->act_size * sizeof(float), cudaMemcpyDeviceToDevice, s));
   if (st == SHAC_OK) st = cuda_ok(cudaStreamSynchronize(s));   // qh is a host temporary
   if (st == SHAC_OK) st = cuda_ok(cudaEventCreate(&e0));
   if (st == SHAC_OK) st = cuda_ok(cudaEventCreate(&e1));
@@ -989,7 +997,11 @@ extern "C" shac_status shac_autotune(shac_batch* b, void* stream, void* ws, int3
   if (st == SHAC_OK) st = measure(&best);
   static const int kLanes[] = {1, 2, 4, 8, 16, 32};
   static const int kWarps[] = {1, 2, 4, 8};
-  for (int gi = 0; gi < n_groups && st == SHAC_OK && !out_of_time(); ++gi) {
+  // a specialised batch keeps the team size its kernels were compiled for
+  // (other team sizes would run the generic kernels, which rank shapes
+  // differently) and searches the warps per CTA with its own kernels
+  const bool specialised = b->spec.key != 0 && b->spec_lanes == b->groups[0].lanes;
+  for (int gi = 0; gi < n_groups && st == SHAC_OK && !out_of_time() && !specialised; ++gi) {
     if (b->groups[gi].N == 0) continue;
     for (int l : kLanes) {
       if (st != SHAC_OK || out_of_time()) break;

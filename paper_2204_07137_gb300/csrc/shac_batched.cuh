@@ -26,10 +26,10 @@ namespace shac {
 
 // Register caps of the batched kernels (forward, adjoint): the live state of
 // the chain carries and of the 32-row dense path fits without spills; the
-// host launches at most 8 warps per CTA (8 x 32 x 208 registers fit an SM's
-// 64 Ki).
+// host launches at most 8 warps per CTA (8 x 32 x 216 registers fit an SM's
+// 64 Ki, and two 4-warp CTAs stay resident per SM).
 #define BATCHED_REGS_FORWARD 184
-#define BATCHED_REGS_ADJOINT 208
+#define BATCHED_REGS_ADJOINT 216
 
 
 struct Team {

@@ -107,8 +107,14 @@ struct DevModel {
 // are odd, so the lanes of a one-lane-per-link pass hit distinct banks.
 constexpr int LREC = 35;    // R 9, P 3, spatial inertia 10, V 6, external wrench 6, pad
 constexpr int LR_R = 0, LR_P = 9, LR_SI = 12, LR_V = 22, LR_FX = 28;
-constexpr int LWORK = 65;   // A 6, F 6, Ic 10, V_bar 6, A_bar 6, F_bar 6, R_bar 9, P_bar 3, pose cotangent to parent 12, pad
-constexpr int LW_A = 0, LW_F = 6, LW_IC = 12, LW_VB = 22, LW_AB = 28, LW_FB = 34, LW_RB = 40, LW_PB = 49, LW_TP = 52;
+// The work record's fields are ordered so that every tree sum of a team runs
+// over one block of consecutive floats: [A, F_bar] (root first, reverse),
+// [Ic, F] (leaves first, forward), [F, A_bar], V_bar and [R_bar, P_bar]
+// (leaves first, reverse).
+constexpr int LWORK = 65;   // A 6, F_bar 6, Ic 10, F 6, A_bar 6, V_bar 6, R_bar 9, P_bar 3, pose cotangent to parent 12, pad
+constexpr int LW_A = 0, LW_FB = 6, LW_IC = 12, LW_F = 22, LW_AB = 28, LW_VB = 34, LW_RB = 40, LW_PB = 49, LW_TP = 52;
+static_assert(LW_FB == LW_A + 6 && LW_F == LW_IC + 10 && LW_AB == LW_F + 6 && LW_PB == LW_RB + 9,
+              "tree-sum blocks must be contiguous");
 
 // ------------------------------------------------------------ accessors --
 // Global-memory scratch: component c of an environment at base[c * stride].
@@ -125,6 +131,55 @@ struct SMem {
 
 __device__ __forceinline__ int lrec(const DevModel& M, int i) { return M.o_LR + LREC * i; }
 __device__ __forceinline__ int lwork(const DevModel& M, int i) { return M.o_LW + LWORK * i; }
+
+// Parent of link i (-1: a root).  A model-specialised build has the parent
+// table as a literal list (SHAC_SPEC_PARENTS), so in a loop over the links that
+// the compiler unrolls, every parent and every scratch address derived from it
+// is a constant; for a link index only known at run time use the table read.
+__device__ __forceinline__ int link_parent(const DevModel& M, int i) {
+#ifdef SHAC_SPEC_PARENTS
+  constexpr int kParent[] = {SHAC_SPEC_PARENTS};
+  (void)M;
+  return kParent[i];
+#else
+  return __ldg(M.parent + i);
+#endif
+}
+
+// Subtree sums of NC consecutive floats of every link's work record starting
+// at field f, one component per lane: x_p += x_i for each link i > 0 with a
+// parent, in descending order.  Links are numbered parent first, so link i's
+// subtree is complete when i is reached; every lane runs the same link
+// sequence (no barrier per tree level, no chain lookups) and the lanes of one
+// link access consecutive words.  A model may have several roots (parent -1).
+// REC: the field is in the link record instead of the work record.
+template <bool REC>
+__device__ __forceinline__ int lbase(const DevModel& M, int i) { return REC ? lrec(M, i) : lwork(M, i); }
+
+template <int NC, bool REC = false, class Mem>
+__device__ __forceinline__ void subtree_sums(const DevModel& M, const Mem& w, int f, int lane, int nl) {
+  for (int c = lane; c < NC; c += nl) {
+#pragma unroll
+    for (int i = M.L - 1; i > 0; --i) {
+      const int p = link_parent(M, i);
+      if (p >= 0) w[lbase<REC>(M, p) + f + c] += w[lbase<REC>(M, i) + f + c];
+    }
+  }
+}
+
+// Ancestor sums, the root-first counterpart: x_i += x_p for each link i > 0
+// with a parent, in ascending order (the parent's value is final when i is
+// reached).
+template <int NC, bool REC = false, class Mem>
+__device__ __forceinline__ void ancestor_sums(const DevModel& M, const Mem& w, int f, int lane, int nl) {
+  for (int c = lane; c < NC; c += nl) {
+#pragma unroll
+    for (int i = 1; i < M.L; ++i) {
+      const int p = link_parent(M, i);
+      if (p >= 0) w[lbase<REC>(M, i) + f + c] += w[lbase<REC>(M, p) + f + c];
+    }
+  }
+}
 
 __device__ __forceinline__ void team_sync(int nl) {
   if (nl > 1) __syncwarp();
@@ -411,6 +466,68 @@ __device__ __forceinline__ void lk_kin(const DevModel& M, const Mem& w, int i, K
   c.R = R; c.P = P; c.Vw = Vw; c.Vv = Vv; c.aw = aw; c.av = av;
 }
 
+// Team form of sweep 1: only the world poses flow along the chains (lk_pose,
+// R_i = R_p R_local, P_i = P_p + R_p P_local, the parent's pose carried in
+// registers); the rest of lk_kin is a pass per link and two ancestor sums,
+// since V_i = V_p + u_i and A_i = A_p + V_i x u_i (the roots' A_p: -g) are
+// sums of terms of each link along its path from the root.
+struct PoseCarry {
+  M33 R;
+  V3 P;
+};
+template <class Mem>
+__device__ __forceinline__ void lk_pose(const DevModel& M, const Mem& w, int i, bool root, PoseCarry& c) {
+  M33 R = ldm(w, lrec(M, i) + LR_R);
+  V3 P = ld3(w, lrec(M, i) + LR_P);
+  if (!root) {
+    P = c.P + mul(c.R, P);
+    R = mul(c.R, R);
+  }
+  stm(w, lrec(M, i) + LR_R, R);
+  st3(w, lrec(M, i) + LR_P, P);
+  c.R = R;
+  c.P = P;
+}
+// Link i's motion-subspace columns (as in lk_kin) and its joint velocity u_i,
+// the own term of V_i, stored in the V field and, for lk_bias_acc_own, in the
+// F_bar field (unused by the forward pass).
+template <class Mem>
+__device__ __forceinline__ void lk_subspace_vel(const DevModel& M, const Mem& w, int i) {
+  const int jt = __ldg(M.jtype + i), d0 = __ldg(M.ds + i), nd = __ldg(M.nd + i);
+  const M33 R = ldm(w, lrec(M, i) + LR_R);
+  const V3 P = ld3(w, lrec(M, i) + LR_P);
+  V3 uw = v3(0.f, 0.f, 0.f), uv = v3(0.f, 0.f, 0.f);
+  auto subspace = [&](int k, V3 sw, V3 sv) {
+    st3(w, M.o_S + 6 * (d0 + k), sw);
+    st3(w, M.o_S + 6 * (d0 + k) + 3, sv);
+    const float qd = w[M.o_QD + d0 + k];
+    uw = uw + qd * sw;
+    uv = uv + qd * sv;
+  };
+  if (jt == J_FREE) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) subspace(k, col(R, k), cross(P, col(R, k)));
+#pragma unroll
+    for (int k = 0; k < 3; ++k) subspace(3 + k, v3(0.f, 0.f, 0.f), col(R, k));
+  } else if (nd == 1) {
+    const V3 a = mul(R, cld3(M.axis + 3 * i));
+    if (jt == J_REV) subspace(0, a, cross(P, a));
+    else subspace(0, v3(0.f, 0.f, 0.f), a);
+  }
+  st3(w, lrec(M, i) + LR_V, uw); st3(w, lrec(M, i) + LR_V + 3, uv);
+  st3(w, lwork(M, i) + LW_FB, uw); st3(w, lwork(M, i) + LW_FB + 3, uv);
+}
+// The own term of A_i after the velocity sums: V_i x u_i, and -g at a root.
+template <class Mem>
+__device__ __forceinline__ void lk_bias_acc_own(const DevModel& M, const Mem& w, int i) {
+  const V3 Vw = ld3(w, lrec(M, i) + LR_V), Vv = ld3(w, lrec(M, i) + LR_V + 3);
+  const V3 uw = ld3(w, lwork(M, i) + LW_FB), uv = ld3(w, lwork(M, i) + LW_FB + 3);
+  const V3 aw = cross(Vw, uw);
+  V3 av = cross(Vw, uv) + cross(Vv, uw);
+  if (__ldg(M.parent + i) < 0) av = av + v3(-M.grav[0], -M.grav[1], -M.grav[2]);
+  st3(w, lwork(M, i) + LW_A, aw); st3(w, lwork(M, i) + LW_A + 3, av);
+}
+
 // lk_local: the spatial inertia about the reference point (m, h = m c, Io),
 // the contact forces of link i and its local force
 // F_i = I_i A_i + V_i x* (I_i V_i) - Fext_i, from the pose, velocity and
@@ -429,10 +546,12 @@ __device__ __forceinline__ void lk_local(const DevModel& M, const Mem& w, int i)
   const float ixx = Iw.m[0] + m * (cc - c.x * c.x), iyy = Iw.m[4] + m * (cc - c.y * c.y);
   const float izz = Iw.m[8] + m * (cc - c.z * c.z), ixy = Iw.m[1] - m * c.x * c.y;
   const float ixz = Iw.m[2] - m * c.x * c.z, iyz = Iw.m[5] - m * c.y * c.z;
-  {
-    const int o = lrec(M, i) + LR_SI;
+  {   // the link's own spatial inertia, in the record and as the start of its composite inertia
+    const int o = lrec(M, i) + LR_SI, oc = lwork(M, i) + LW_IC;
     w[o] = m; st3(w, o + 1, h);
     w[o + 4] = ixx; w[o + 5] = iyy; w[o + 6] = izz; w[o + 7] = ixy; w[o + 8] = ixz; w[o + 9] = iyz;
+    w[oc] = m; st3(w, oc + 1, h);
+    w[oc + 4] = ixx; w[oc + 5] = iyy; w[oc + 6] = izz; w[oc + 7] = ixy; w[oc + 8] = ixz; w[oc + 9] = iyz;
   }
   auto imul = [&](V3 xw, V3 xv, V3& yn, V3& yf) {
     yn = v3(ixx * xw.x + ixy * xw.y + ixz * xw.z, ixy * xw.x + iyy * xw.y + iyz * xw.z,
@@ -488,17 +607,44 @@ template <class Mem>
 __device__ void sw_forward(const DevModel& M, const Mem& w, int lane, int nl) {
   for (int i = lane; i < M.L; i += nl) lk_joint_local(M, w, i);
   team_sync(nl);
-  for (int l = 0; l < M.nlev; ++l) {
-    for (int ii = __ldg(M.lvl_ptr + l) + lane; ii < __ldg(M.lvl_ptr + l + 1); ii += nl) {
-      const int hd = __ldg(M.lvl_link + ii), tl = __ldg(M.chain_tail + hd);
-      KinCarry c;
-      kin_parent(M, w, __ldg(M.parent + hd), c);
-      for (int i = hd;; i = chain_next(M, i)) {
-        lk_kin(M, w, i, c);
-        if (i == tl) break;
+  if (nl > 1) {   // a team: the poses along the chains, the rest per link and by ancestor sums
+    for (int l = 0; l < M.nlev; ++l) {
+      for (int ii = __ldg(M.lvl_ptr + l) + lane; ii < __ldg(M.lvl_ptr + l + 1); ii += nl) {
+        const int hd = __ldg(M.lvl_link + ii), tl = __ldg(M.chain_tail + hd), p = __ldg(M.parent + hd);
+        PoseCarry c;
+        if (p >= 0) {
+          c.R = ldm(w, lrec(M, p) + LR_R);
+          c.P = ld3(w, lrec(M, p) + LR_P);
+        }
+        bool root = p < 0;
+        for (int i = hd;; i = chain_next(M, i)) {
+          lk_pose(M, w, i, root, c);
+          root = false;
+          if (i == tl) break;
+        }
+      }
+      team_sync(nl);
+    }
+    for (int i = lane; i < M.L; i += nl) lk_subspace_vel(M, w, i);
+    team_sync(nl);
+    ancestor_sums<6, true>(M, w, LR_V, lane, nl);
+    team_sync(nl);
+    for (int i = lane; i < M.L; i += nl) lk_bias_acc_own(M, w, i);
+    team_sync(nl);
+    ancestor_sums<6>(M, w, LW_A, lane, nl);
+    team_sync(nl);
+  } else {        // one thread: chain walks carrying pose, velocity and acceleration
+    for (int l = 0; l < M.nlev; ++l) {
+      for (int ii = __ldg(M.lvl_ptr + l); ii < __ldg(M.lvl_ptr + l + 1); ++ii) {
+        const int hd = __ldg(M.lvl_link + ii), tl = __ldg(M.chain_tail + hd);
+        KinCarry c;
+        kin_parent(M, w, __ldg(M.parent + hd), c);
+        for (int i = hd;; i = chain_next(M, i)) {
+          lk_kin(M, w, i, c);
+          if (i == tl) break;
+        }
       }
     }
-    team_sync(nl);
   }
   for (int i = lane; i < M.L; i += nl) lk_local(M, w, i);
   team_sync(nl);
@@ -537,16 +683,16 @@ struct GatherCarry {
   float ic[10];
 };
 
-// F_i += sum_children F_c (total forces) and the composite inertia
-// Ic_i = I_i + sum_children Ic_c (CRBA part 1).  Inside a chain the only child
-// is the link walked before (carried in g); the chain's tail reads its
-// children from scratch.
+// F_i += sum_children F_c (total forces) and Ic_i += sum_children Ic_c
+// (composite inertias, CRBA part 1; lk_local starts Ic_i at the link's own
+// inertia).  Inside a chain the only child is the link walked before (carried
+// in g); the chain's tail reads its children from scratch.
 template <class Mem>
 __device__ __forceinline__ void lk_gather(const DevModel& M, const Mem& w, int i, bool tail, GatherCarry& g) {
   V3 fn = ld3(w, lwork(M, i) + LW_F), ff = ld3(w, lwork(M, i) + LW_F + 3);
   float ic[10];
 #pragma unroll
-  for (int k = 0; k < 10; ++k) ic[k] = w[lrec(M, i) + LR_SI + k];
+  for (int k = 0; k < 10; ++k) ic[k] = w[lwork(M, i) + LW_IC + k];
   if (tail) {
     const int c0 = __ldg(M.ch_ptr + i), c1 = __ldg(M.ch_ptr + i + 1);
     for (int kk = c0; kk < c1; ++kk) {
@@ -572,11 +718,18 @@ __device__ __forceinline__ void lk_gather(const DevModel& M, const Mem& w, int i
   for (int k = 0; k < 10; ++k) g.ic[k] = ic[k];
 }
 
-// Sweep 2, leaves first: total forces and composite inertias.
+// Sweep 2, leaves first: total forces and composite inertias (Ic and F are the
+// 16 consecutive floats from LW_IC).  A team sums them one component per lane;
+// a single thread (PLAIN form) walks the chains with register carries.
 template <class Mem>
 __device__ void sw_gather(const DevModel& M, const Mem& w, int lane, int nl) {
+  if (nl > 1) {
+    subtree_sums<16>(M, w, LW_IC, lane, nl);
+    team_sync(nl);
+    return;
+  }
   for (int l = M.nlev - 1; l >= 0; --l) {
-    for (int ii = __ldg(M.lvl_ptr + l) + lane; ii < __ldg(M.lvl_ptr + l + 1); ii += nl) {
+    for (int ii = __ldg(M.lvl_ptr + l); ii < __ldg(M.lvl_ptr + l + 1); ++ii) {
       const int hd = __ldg(M.lvl_link + ii), tl = __ldg(M.chain_tail + hd);
       GatherCarry g;
       for (int i = tl;; i = __ldg(M.parent + i)) {
@@ -584,7 +737,6 @@ __device__ void sw_gather(const DevModel& M, const Mem& w, int lane, int nl) {
         if (i == hd) break;
       }
     }
-    team_sync(nl);
   }
 }
 
@@ -692,15 +844,18 @@ __device__ __forceinline__ float two_sum(float a, float b, float& e) {
 // accumulation is carried in o_QC/o_QDC (zeroed at every step start) and fed
 // back into the next substep's update, so a step of K substeps rounds its
 // state once.
+// The velocity update of DOF d (first, for every DOF) ...
+template <class Mem>
+__device__ __forceinline__ void dof_integrate(const DevModel& M, const Mem& w, int d) {
+  float e;
+  const float y = M.h * w[M.o_QDD + d] + w[M.o_QDC + d];
+  w[M.o_QD + d] = two_sum(w[M.o_QD + d], y, e);
+  w[M.o_QDC + d] = e;
+}
+// ... then the position update of link i's joint from the new velocities.
 template <class Mem>
 __device__ __forceinline__ void lk_integrate(const DevModel& M, const Mem& w, int i) {
-  const int jt = __ldg(M.jtype + i), s = __ldg(M.qs + i), d0 = __ldg(M.ds + i), nd = __ldg(M.nd + i);
-  for (int d = d0; d < d0 + nd; ++d) {
-    float e;
-    const float y = M.h * w[M.o_QDD + d] + w[M.o_QDC + d];
-    w[M.o_QD + d] = two_sum(w[M.o_QD + d], y, e);
-    w[M.o_QDC + d] = e;
-  }
+  const int jt = __ldg(M.jtype + i), s = __ldg(M.qs + i), d0 = __ldg(M.ds + i);
   if (jt == J_FREE) {
     const M33 R = ldm(w, lrec(M, i) + LR_R);
     const V3 dp = M.h * mul(R, ld3(w, M.o_QD + d0 + 3)) + M.h * mul(R, ld3(w, M.o_QDC + d0 + 3));
@@ -727,6 +882,8 @@ __device__ __forceinline__ void lk_integrate(const DevModel& M, const Mem& w, in
 
 template <class Mem>
 __device__ void st_integrate(const DevModel& M, const Mem& w, int lane, int nl) {
+  for (int d = lane; d < M.nv; d += nl) dof_integrate(M, w, d);
+  team_sync(nl);
   for (int i = lane; i < M.L; i += nl) lk_integrate(M, w, i);
   team_sync(nl);
 }
@@ -762,19 +919,23 @@ __device__ __forceinline__ void chol_trailing(float (&row)[NM], float lik, int l
   (chol_update<K + 1 + J, NM>(row, lik, lane, nl), ...);
 }
 // Column K: L_KK = sqrt(pivot) (lane K), L_iK = M_iK / L_KK (lanes i > K).
+// Every lane also keeps its own diagonal entry in `diag`, updated with its own
+// L_iK (the same multiply-adds the trailing update applies to row[i] on lane
+// i), so the next column's pivot is broadcast from a register that does not
+// wait for this column's shuffles.
 template <int K, int NM>
-__device__ __forceinline__ void chol_column(float (&row)[NM], float& inv_diag, int lane, int nl) {
-  const float rk = row[K];
-  const float inv = rsqrtf(__shfl_sync(0xffffffffu, rk, K, nl));
-  const float lik = rk * inv;
+__device__ __forceinline__ void chol_column(float (&row)[NM], float& diag, float& inv_diag, int lane, int nl) {
+  const float inv = rsqrtf(__shfl_sync(0xffffffffu, diag, K, nl));
+  const float lik = row[K] * inv;
   if (lane >= K) row[K] = lik;
   if (lane == K) inv_diag = inv;
+  if (lane > K) diag = fmaf(-lik, lik, diag);
   chol_trailing<K, NM>(row, lik, lane, nl, make_iseq<NM - K - 1>{});
 }
 template <int NM, int... K>
-__device__ __forceinline__ void chol_columns(float (&row)[NM], float& inv_diag, int lane, int nl,
+__device__ __forceinline__ void chol_columns(float (&row)[NM], float& diag, float& inv_diag, int lane, int nl,
                                              iseq<K...>) {
-  (chol_column<K, NM>(row, inv_diag, lane, nl), ...);
+  (chol_column<K, NM>(row, diag, inv_diag, lane, nl), ...);
 }
 
 // Forward substitution y = L^{-1} b, step K: lane a holds b_a, row a of L in
@@ -811,17 +972,20 @@ __device__ __forceinline__ void bsub(const DevModel& M, const Mem& w, float inv_
 
 // Row a of M (CRBA part 2) into registers; padding rows are identity rows.
 template <int B, int NM, class Mem>
-__device__ __forceinline__ void row_entry(const DevModel& M, const Mem& w, float (&row)[NM], unsigned mask, V3 fn,
-                                          V3 ff, float arm, int lane) {
+__device__ __forceinline__ void row_entry(const DevModel& M, const Mem& w, float (&row)[NM], float& diag,
+                                          unsigned mask, V3 fn, V3 ff, float arm, int lane) {
   // every lane reads column B's subspace (a broadcast; padding columns read
   // other scratch) and keeps the product only where DOF B moves an ancestor
   const float p = dot(ld3(w, M.o_S + 6 * B), fn) + dot(ld3(w, M.o_S + 6 * B + 3), ff);
   float v = ((mask >> B) & 1u) ? p : 0.f;
-  if (B == lane) v += arm;
+  if (B == lane) {
+    v += arm;
+    diag = v;
+  }
   row[B] = v;
 }
 template <int NM, class Mem, int... B>
-__device__ __forceinline__ void row_assemble(const DevModel& M, const Mem& w, float (&row)[NM], int lane,
+__device__ __forceinline__ void row_assemble(const DevModel& M, const Mem& w, float (&row)[NM], float& diag, int lane,
                                              iseq<B...>) {
   V3 fn = v3(0.f, 0.f, 0.f), ff = v3(0.f, 0.f, 0.f);
   unsigned mask = 0u;
@@ -832,7 +996,7 @@ __device__ __forceinline__ void row_assemble(const DevModel& M, const Mem& w, fl
     mask = __ldg(M.anc_mask + lane);
   }
   const float arm = own ? __ldg(M.arm + lane) : 1.f;
-  (row_entry<B, NM>(M, w, row, mask, fn, ff, arm, lane), ...);
+  (row_entry<B, NM>(M, w, row, diag, mask, fn, ff, arm, lane), ...);
 }
 template <int B, int NM, class Mem>
 __device__ __forceinline__ void row_store_entry(const DevModel& M, const Mem& w, const float (&row)[NM], int lane) {
@@ -862,9 +1026,10 @@ __device__ __forceinline__ void dense_substep(const DevModel& M, const Mem& w, i
   using Seq = make_iseq<NM>;
   const bool own = lane < M.nv;
   float row[NM];
-  row_assemble<NM>(M, w, row, lane, Seq{});
+  float diag = 1.f;
+  row_assemble<NM>(M, w, row, diag, lane, Seq{});
   float inv_diag = 1.f;
-  chol_columns<NM>(row, inv_diag, lane, nl, Seq{});
+  chol_columns<NM>(row, diag, inv_diag, lane, nl, Seq{});
   row_store<NM>(M, w, row, lane, Seq{});
   if (own) w[M.o_LD + lane] = inv_diag;
   team_sync(nl);
@@ -1096,6 +1261,17 @@ __device__ __forceinline__ void lk_adj_acc(const DevModel& M, const Mem& w, int 
   c.aw = aw; c.av = av; c.nb = nb; c.fb = fb;
 }
 
+// Team form of adjoint sweep 1: link i's own terms of (A, F_bar) (its DOFs'
+// S qdd and -lambda S, V_i x u_i and, for a root, the base acceleration -g),
+// which ancestor_sums over [A, F_bar] then turn into the recursion's values.
+template <class Mem>
+__device__ __forceinline__ void lk_adj_acc_own(const DevModel& M, const Mem& w, int i) {
+  AccCarry c;
+  acc_parent(M, w, -1, c);
+  if (__ldg(M.parent + i) >= 0) c.av = v3(0.f, 0.f, 0.f);
+  lk_adj_acc(M, w, i, c);
+}
+
 // Cotangent of the spatial inertia from y = I x (y_bar given): h_bar and the
 // (full 3 x 3) cotangent G of Io, accumulated in registers (no mass
 // cotangent: masses are constants).
@@ -1128,7 +1304,7 @@ __device__ __forceinline__ void dof_adj_force(const DevModel& M, const Mem& w, i
 // through h = m c, Io = R Ic R^T + m(|c|^2 1 - c c^T), c = P + R com to the
 // pose); and the reverse of link i's contacts (their external wrench enters
 // F_i with a minus).  Stores link i's V_bar, R_bar and P_bar accumulators.
-template <class Mem>
+template <bool KEEP_RLOCAL, class Mem>
 __device__ __forceinline__ void lk_adj_local(const DevModel& M, const Mem& w, int i) {
   const int jt = __ldg(M.jtype + i);
   const int osi = lrec(M, i) + LR_SI;
@@ -1242,8 +1418,9 @@ __device__ __forceinline__ void lk_adj_local(const DevModel& M, const Mem& w, in
   st3(w, lwork(M, i) + LW_PB, Pb);
   stm(w, lwork(M, i) + LW_RB, Rb);
   // joint-local rotation R_local = jrot Rot(axis, q) of a revolute joint with
-  // a parent, kept in link i's pose-cotangent slot until the leaves-first sweep replaces it
-  if (jt == J_REV && __ldg(M.parent + i) >= 0)
+  // a parent, kept in link i's pose-cotangent slot until the leaves-first
+  // chain sweep replaces it (the team form's world-frame sums need none)
+  if (KEEP_RLOCAL && jt == J_REV && __ldg(M.parent + i) >= 0)
     stm(w, lwork(M, i) + LW_TP, mul(cldm(M.jrot + 9 * i), axis_angle(cld3(M.axis + 3 * i), w[M.o_Q + __ldg(M.qs + i)])));
 }
 
@@ -1355,10 +1532,7 @@ __device__ __forceinline__ void lk_adj_bwd(const DevModel& M, const Mem& w, int 
   const V3 ax = cld3(M.axis + 3 * i);
   if (jt == J_FREE) {
     // a free joint is the root: its six DOF terms feed only its own q_bar, so
-    // they run after the sweep, one DOF per lane (root_dof_terms); keep the
-    // velocity cotangent sums they need
-    st3(w, M.o_RDB, ubw + vw);
-    st3(w, M.o_RDB + 3, ubv + vv);
+    // they run after the sweep, one DOF per lane (root_dof_terms)
   } else if (nd == 1) {
     const float wd = -lam1;
     w[M.o_QDB + d0] = qdb1 + (dot(s1w, ubw + vw) + dot(s1v, ubv + vv));
@@ -1395,6 +1569,65 @@ __device__ __forceinline__ void lk_adj_bwd(const DevModel& M, const Mem& w, int 
   }
 }
 
+// Team form of adjoint sweep 2 (leaves first): every recursion of lk_adj_bwd
+// as subtree sums of the links' own terms.  F_total and A_bar are sums of the
+// links' own values; V_bar_i = V_bar_own_i + (terms of u_i and A_bar_i) + the
+// children's V_bar is a sum of lk_adj_vbar_own's terms.  The pose cotangents
+// pass through the joint transforms (R_i = R_p R_local, P_i = P_p + R_p P_local):
+// with the world-frame moment Q_k = R_bar_k R_k^T + P_bar_k P_k^T of each link's
+// own cotangents, the total of link p is
+//   R_bar_p = (sum_{k in sub(p)} Q_k - (sum_{k in sub(p)} P_bar_k) P_p^T) R_p,
+//   P_bar_p = sum_{k in sub(p)} P_bar_k,
+// because R_local^T R_p^T = R_c^T and R_p P_local = P_c - P_p telescope along
+// every path of the subtree; so no transform runs along the tree.
+template <class Mem>
+__device__ __forceinline__ void lk_adj_vbar_own(const DevModel& M, const Mem& w, int i) {
+  V3 uw, uv;
+  joint_vel(M, w, i, uw, uv);
+  const V3 an = ld3(w, lwork(M, i) + LW_AB), af = ld3(w, lwork(M, i) + LW_AB + 3);
+  add3(w, lwork(M, i) + LW_VB, cross(uw, an) + cross(uv, af));
+  add3(w, lwork(M, i) + LW_VB + 3, cross(uw, af));
+}
+
+// After the F, A_bar and V_bar sums: link i's one-DOF joint terms (qd_bar and
+// the subspace cotangent's share of the pose cotangents; a free root's six DOFs
+// run in root_dof_terms), then its moment Q_i over R_bar (P_bar stays).
+template <class Mem>
+__device__ __forceinline__ void lk_adj_pose(const DevModel& M, const Mem& w, int i) {
+  const int ow = lwork(M, i), orc = lrec(M, i);
+  M33 Rb = ldm(w, ow + LW_RB);
+  V3 Pb = ld3(w, ow + LW_PB);
+  const M33 R = ldm(w, orc + LR_R);
+  const V3 P = ld3(w, orc + LR_P);
+  const int jt = __ldg(M.jtype + i), nd = __ldg(M.nd + i);
+  if (jt != J_FREE && nd == 1) {
+    const int d0 = __ldg(M.ds + i);
+    const V3 Fn = ld3(w, ow + LW_F), Ff = ld3(w, ow + LW_F + 3);
+    const V3 an = ld3(w, ow + LW_AB), af = ld3(w, ow + LW_AB + 3);
+    const V3 Vw = ld3(w, orc + LR_V), Vv = ld3(w, orc + LR_V + 3);
+    const V3 s1w = ld3(w, M.o_S + 6 * d0), s1v = ld3(w, M.o_S + 6 * d0 + 3);
+    const float wd = -w[M.o_LAM + d0], qdd1 = w[M.o_QDD + d0], qd1 = w[M.o_QD + d0];
+    const V3 uw = cross(an, Vw) + cross(af, Vv) + ld3(w, ow + LW_VB);
+    const V3 uv = cross(af, Vw) + ld3(w, ow + LW_VB + 3);
+    w[M.o_QDB + d0] += dot(s1w, uw) + dot(s1v, uv);
+    const V3 sbw = wd * Fn + qdd1 * an + qd1 * uw;
+    const V3 sbv = wd * Ff + qdd1 * af + qd1 * uv;
+    const V3 ax = cld3(M.axis + 3 * i);
+    V3 ab;
+    if (jt == J_REV) {   // (a, P x a), a = R ax
+      ab = sbw + cross(sbv, P);
+      Pb = Pb + cross(mul(R, ax), sbv);
+    } else {             // (0, a)
+      ab = sbv;
+    }
+    add_outer(Rb, ab, ax);
+  }
+  M33 Q = mulBT(Rb, R);
+  add_outer(Q, Pb, P);
+  stm(w, ow + LW_RB, Q);
+  st3(w, ow + LW_PB, Pb);
+}
+
 // The free root's DOF d (0..5) after the leaves-first sweep: tau = S^T F_total
 // gives qd_bar_d and the subspace cotangents (sbw, sbv), whose share of the
 // root's rotation cotangent (column d mod 3: (R e_k, P x R e_k) for the body
@@ -1402,9 +1635,12 @@ __device__ __forceinline__ void lk_adj_bwd(const DevModel& M, const Mem& w, int 
 // position cotangent is not needed (the root origin is the reference point).
 template <class Mem>
 __device__ __forceinline__ void root_dof_terms(const DevModel& M, const Mem& w, int d) {
-  const V3 uw = ld3(w, M.o_RDB), uv = ld3(w, M.o_RDB + 3);
   const V3 Fn = ld3(w, lwork(M, 0) + LW_F), Ff = ld3(w, lwork(M, 0) + LW_F + 3);
   const V3 an = ld3(w, lwork(M, 0) + LW_AB), af = ld3(w, lwork(M, 0) + LW_AB + 3);
+  const V3 Vw = ld3(w, lrec(M, 0) + LR_V), Vv = ld3(w, lrec(M, 0) + LR_V + 3);
+  // cotangent of the root's velocity terms: V_bar plus the V x u part of A
+  const V3 uw = cross(an, Vw) + cross(af, Vv) + ld3(w, lwork(M, 0) + LW_VB);
+  const V3 uv = cross(af, Vw) + ld3(w, lwork(M, 0) + LW_VB + 3);
   const float wd = -w[M.o_LAM + d], qdd = w[M.o_QDD + d], qd = w[M.o_QD + d];
   const V3 sw = ld3(w, M.o_S + 6 * d), sv = ld3(w, M.o_S + 6 * d + 3);
   w[M.o_QDB + d] += dot(sw, uw) + dot(sv, uv);
@@ -1417,10 +1653,17 @@ __device__ __forceinline__ void root_dof_terms(const DevModel& M, const Mem& w, 
 // dR/dq = [a]x R with a = R ax; prismatic dP/dq = a; free root: the
 // quaternion's share through R(quat), and the root height receives every
 // contact depth's cotangent (depth = x.z + root height).
-template <class Mem>
+// WORLD: the R_bar slot holds the subtree sum of Q and the P_bar slot that of
+// P_bar (team form); R_bar = (Q - P_bar P^T) R is formed first.
+template <bool WORLD, class Mem>
 __device__ __forceinline__ void lk_adj_qbar(const DevModel& M, const Mem& w, int i) {
   const int jt = __ldg(M.jtype + i), s = __ldg(M.qs + i);
   M33 Rb = ldm(w, lwork(M, i) + LW_RB);
+  if (WORLD) {
+    if (jt == J_FIXED) return;
+    add_outer(Rb, -ld3(w, lwork(M, i) + LW_PB), ld3(w, lrec(M, i) + LR_P));
+    Rb = mul(Rb, ldm(w, lrec(M, i) + LR_R));
+  }
   if (jt == J_FREE) {   // the root origin is the reference point: no position cotangent here
 #pragma unroll
     for (int k = 0; k < 3; ++k) {   // the six DOF terms' shares, column k from DOFs k and 3 + k
@@ -1464,21 +1707,34 @@ __device__ __forceinline__ void st_dynamics_adj(const DevModel& M, const Mem& w,
     team_sync(nl);
     st_solve(M, w, lane, nl, M.o_B, M.o_LAM);
   }
-  for (int l = 0; l < M.nlev; ++l) {
-    for (int ii = __ldg(M.lvl_ptr + l) + lane; ii < __ldg(M.lvl_ptr + l + 1); ii += nl) {
-      const int hd = __ldg(M.lvl_link + ii), tl = __ldg(M.chain_tail + hd);
-      AccCarry c;
-      acc_parent(M, w, __ldg(M.parent + hd), c);
-      for (int i = hd;; i = chain_next(M, i)) {
-        lk_adj_acc(M, w, i, c);
-        if (i == tl) break;
+  // root first: accelerations with the solved qdd and force cotangents (a
+  // team: each link's own terms, then ancestor sums; one thread: chain walks
+  // with register carries)
+  if (nl > 1) {
+    for (int i = lane; i < M.L; i += nl) lk_adj_acc_own(M, w, i);
+    team_sync(nl);
+    ancestor_sums<12>(M, w, LW_A, lane, nl);
+    team_sync(nl);
+  } else {
+    for (int l = 0; l < M.nlev; ++l) {
+      for (int ii = __ldg(M.lvl_ptr + l); ii < __ldg(M.lvl_ptr + l + 1); ++ii) {
+        const int hd = __ldg(M.lvl_link + ii), tl = __ldg(M.chain_tail + hd);
+        AccCarry c;
+        acc_parent(M, w, __ldg(M.parent + hd), c);
+        for (int i = hd;; i = chain_next(M, i)) {
+          lk_adj_acc(M, w, i, c);
+          if (i == tl) break;
+        }
       }
     }
-    team_sync(nl);
   }
   // one pass: links from the first lane up, DOFs' joint forces from the last
   // lane down (a free root's six DOFs do not load the root's lane)
-  for (int i = lane; i < M.L; i += nl) lk_adj_local(M, w, i);
+  if (nl > 1) {
+    for (int i = lane; i < M.L; i += nl) lk_adj_local<false>(M, w, i);
+  } else {
+    for (int i = 0; i < M.L; ++i) lk_adj_local<true>(M, w, i);
+  }
   for (int d = nl - 1 - lane; d < M.nv; d += nl) dof_adj_force(M, w, d);
   team_sync(nl);
   if (M.nseg > 0) {
@@ -1525,8 +1781,27 @@ __device__ __forceinline__ void st_dynamics_adj(const DevModel& M, const Mem& w,
     }
     team_sync(nl);
   }
+  if (nl > 1) {
+    // leaves first as subtree sums of world-frame terms (lk_adj_vbar_own,
+    // lk_adj_pose): F_total and A_bar, V_bar, then the pose moments
+    subtree_sums<12>(M, w, LW_F, lane, nl);
+    team_sync(nl);
+    for (int i = lane; i < M.L; i += nl) lk_adj_vbar_own(M, w, i);
+    team_sync(nl);
+    subtree_sums<6>(M, w, LW_VB, lane, nl);
+    team_sync(nl);
+    for (int i = lane; i < M.L; i += nl) lk_adj_pose(M, w, i);
+    if (M.root_free)   // the root's DOFs on the lanes counted down from the last
+      for (int d = nl - 1 - lane; d < 6; d += nl) root_dof_terms(M, w, d);
+    team_sync(nl);
+    subtree_sums<12>(M, w, LW_RB, lane, nl);
+    team_sync(nl);
+    for (int i = lane; i < M.L; i += nl) lk_adj_qbar<true>(M, w, i);
+    team_sync(nl);
+    return;
+  }
   for (int l = M.nlev - 1; l >= 0; --l) {
-    for (int ii = __ldg(M.lvl_ptr + l) + lane; ii < __ldg(M.lvl_ptr + l + 1); ii += nl) {
+    for (int ii = __ldg(M.lvl_ptr + l); ii < __ldg(M.lvl_ptr + l + 1); ++ii) {
       const int hd = __ldg(M.lvl_link + ii), tl = __ldg(M.chain_tail + hd);
       BwdCarry g;
       for (int i = tl;; i = __ldg(M.parent + i)) {
@@ -1534,14 +1809,10 @@ __device__ __forceinline__ void st_dynamics_adj(const DevModel& M, const Mem& w,
         if (i == hd) break;
       }
     }
-    team_sync(nl);
   }
-  if (M.root_free) {
-    for (int d = lane; d < 6; d += nl) root_dof_terms(M, w, d);
-    team_sync(nl);
-  }
-  for (int i = lane; i < M.L; i += nl) lk_adj_qbar(M, w, i);
-  team_sync(nl);
+  if (M.root_free)
+    for (int d = 0; d < 6; ++d) root_dof_terms(M, w, d);
+  for (int i = 0; i < M.L; ++i) lk_adj_qbar<false>(M, w, i);
 }
 
 // One reverse substep: o_Q/o_QD hold the substep start state, o_QB/o_QDB the

@@ -6,7 +6,8 @@
 // the address arithmetic around it.  For one model and one launch shape those
 // values are constants: this file writes them into the kernels' source as
 // literals (every `M.<field>` of the device code becomes a number; the launch
-// shape comes in through the SHAC_SPEC_* macros of shac_batched.cuh), compiles
+// shape comes in through the SHAC_SPEC_* macros of shac_batched.cuh, the link
+// parents through SHAC_SPEC_PARENTS of shac_device.cuh), compiles
 // the forward and adjoint kernels with NVRTC for the device's architecture and
 // loads them with the runtime's library API.  The sources are the library's
 // own device files, embedded at build time (shac_jit_sources.cpp, written by
@@ -61,11 +62,19 @@ std::string with_literals(const char* src, const DevModel& m) {
   return s;
 }
 
-std::string spec_string(int device, const DevModel& m, int lanes, int rows, int stride) {
+// the parent list as a C initialiser list ("-1,0,0,1")
+std::string parent_list(const std::vector<int>& parent) {
+  std::string s;
+  for (size_t i = 0; i < parent.size(); ++i) s += (i ? "," : "") + std::to_string(parent[i]);
+  return s;
+}
+
+std::string spec_string(int device, const DevModel& m, const std::vector<int>& parent, int lanes, int rows,
+                        int stride) {
   std::string s = "dev" + std::to_string(device) + ";lanes" + std::to_string(lanes) + ";rows" +
                   std::to_string(rows) + ";stride" + std::to_string(stride);
   for (const Field& f : kFields) s += ";" + std::string(f.name) + "=" + std::to_string(m.*(f.member));
-  return s;
+  return s + ";parents=" + parent_list(parent);
 }
 
 // FNV-1a; 0 is reserved for the generic kernels
@@ -80,9 +89,10 @@ std::map<std::string, JitKernels> g_cache;
 
 }  // namespace
 
-shac_status jit_kernels(int device, const DevModel& m, int lanes, int rows, int stride, JitKernels* out,
-                        std::string* log) {
-  const std::string spec = spec_string(device, m, lanes, rows, stride);
+shac_status jit_kernels(int device, const DevModel& m, const std::vector<int>& parent, int lanes, int rows,
+                        int stride, JitKernels* out, std::string* log) {
+  if ((int)parent.size() != m.L) return SHAC_ERR_INVALID_ARG;
+  const std::string spec = spec_string(device, m, parent, lanes, rows, stride);
   std::lock_guard<std::mutex> lock(g_mutex);
   auto it = g_cache.find(spec);
   if (it != g_cache.end()) { *out = it->second; return SHAC_OK; }
@@ -111,7 +121,8 @@ shac_status jit_kernels(int device, const DevModel& m, int lanes, int rows, int 
   std::snprintf(lbuf, sizeof lbuf, "-DSHAC_SPEC_LANES=%d", lanes);
   std::snprintf(rbuf, sizeof rbuf, "-DSHAC_SPEC_ROWS=%d", rows);
   std::snprintf(sbuf, sizeof sbuf, "-DSHAC_SPEC_STRIDE=%d", stride);
-  const char* opts[] = {arch.c_str(), "-std=c++17", "-lineinfo", kbuf, lbuf, rbuf, sbuf};
+  const std::string pdef = "-DSHAC_SPEC_PARENTS=" + parent_list(parent);
+  const char* opts[] = {arch.c_str(), "-std=c++17", "-lineinfo", kbuf, lbuf, rbuf, sbuf, pdef.c_str()};
   const nvrtcResult cr = nvrtcCompileProgram(prog, (int)(sizeof opts / sizeof opts[0]), opts);
   if (cr != NVRTC_SUCCESS) {
     if (log) {

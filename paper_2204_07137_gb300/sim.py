@@ -74,18 +74,32 @@ class Simulator:
         _lib.check(_lib.load().shac_batch_set_window_tape(self.batch, int(bool(keep))), "shac_batch_set_window_tape")
         self._alloc_workspace()
 
-    def autotune_native(self, budget_ms: int = 2000, stream=None):
+    def autotune_native(self, budget_ms: int = 2000, stream=None, q0=None, qd0=None, act=None):
         """The library's own measured launch-shape search (shac_autotune):
         lanes per environment for each group, then warps per CTA, timed as short
-        windows from the rest configuration; the fastest shape stays applied.
-        The search's buffers are a temporary torch allocation of
-        shac_autotune_workspace_bytes.  Synchronises; not for a stream capture."""
+        windows (min(h_max, 8) steps) from q0, qd0 with actions act (CUDA float32
+        tensors in the window calls' layouts; act's first min(h_max, 8) steps are
+        used), or from the rest configuration where one is None; the fastest
+        shape stays applied (after specialize(): the team size stays, the warps
+        per CTA are searched with the specialised kernels).  The search's buffers
+        are a temporary torch allocation of shac_autotune_workspace_bytes.
+        Synchronises; not for a stream capture."""
         L = _lib.load()
+        h = min(self.h_max, 8)
+
+        def ptr(t, n):
+            if t is None:
+                return None
+            t = t.reshape(-1)
+            if t.dtype != torch.float32 or not t.is_cuda or not t.is_contiguous() or t.numel() < n:
+                raise ValueError("autotune inputs must be contiguous CUDA float32 tensors of the window layout")
+            return ctypes.c_void_p(t.data_ptr())
+        args = (ptr(q0, self.q_size), ptr(qd0, self.qd_size), ptr(act, h * self.act_size))
         nbytes = int(L.shac_autotune_workspace_bytes(self.batch))
         tmp = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=self.device)
         assert tmp.data_ptr() % 256 == 0
-        _lib.check(L.shac_autotune(self.batch, self._stream(stream), ctypes.c_void_p(tmp.data_ptr()), int(budget_ms)),
-                   "shac_autotune")
+        _lib.check(L.shac_autotune(self.batch, self._stream(stream), ctypes.c_void_p(tmp.data_ptr()), int(budget_ms),
+                                   *args), "shac_autotune")
         del tmp
         self._alloc_workspace()
         return [self.get_launch(g) for g in range(len(self.groups))]

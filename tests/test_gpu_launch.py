@@ -71,9 +71,11 @@ def _window_inputs(sim, h):
 @pytest.mark.parametrize("tape", [False, True])
 def test_native_autotune_keeps_a_valid_shape(tape):
     """shac_autotune (the library's measured search) on a heterogeneous batch,
-    with and without the window tape: a valid shape is left applied, the
-    windows it times (in the caller's buffer of shac_autotune_workspace_bytes)
-    do not disturb the caller's inputs, and the retuned batch gives the same
+    with and without the window tape (timed from the caller's window inputs
+    with the tape, from the rest configuration without): a valid shape is left
+    applied, the windows it times (in the caller's buffer of
+    shac_autotune_workspace_bytes) do not disturb the caller's inputs, and the
+    retuned batch gives the same
     window up to FP32 reassociation inside a team; a non-positive budget is
     rejected."""
     import numpy as np
@@ -89,7 +91,7 @@ def test_native_autotune_keeps_a_valid_shape(tape):
     assert L.shac_autotune_workspace_bytes(tuned.batch) > L.shac_batch_workspace_bytes(tuned.batch)
     q0, qd0, act = _window_inputs(ref, 2)
     keep = [t.clone() for t in (q0, qd0, act)]
-    shapes = tuned.autotune_native(budget_ms=5000)
+    shapes = tuned.autotune_native(budget_ms=5000, **({"q0": q0, "qd0": qd0, "act": act} if tape else {}))
     assert len(shapes) == 2
     assert all(l in LANES and w in WARPS for l, w in shapes)
     assert all(torch.equal(a, b) for a, b in zip(keep, (q0, qd0, act)))

@@ -133,3 +133,23 @@ def test_specialisation_refuses_what_it_does_not_cover():
     sim.specialize(True)
     sim.specialize(False)
     assert _lib.load().shac_batch_specialize(sim.batch, 2) == 1   # SHAC_ERR_INVALID_ARG
+
+
+def test_autotune_on_a_specialised_batch_keeps_its_team_size():
+    """After specialisation the launch-shape search keeps the team size the
+    kernels were compiled for and only moves the warps per CTA; the window it
+    leaves behind computes what the generic kernels compute."""
+    from paper_2204_07137_gb300.sim import Simulator
+    m, N, h = I.ant(), 96, 4
+    spc = Simulator([(m, N)], form="batched", h_max=h)
+    spc.set_launch(0, 16, 4)
+    spc.specialize()
+    shape = spc.autotune_native(budget_ms=3000)
+    assert shape[0][0] == 16 and shape[0][1] in (1, 2, 4, 8)
+    gen = Simulator([(m, N)], form="batched", h_max=h)
+    gen.set_launch(0, 16, 4)
+    _, f, g = _window(spc, m, N, h, 11)
+    _, fg, gg = _window(gen, m, N, h, 11)
+    assert spc.status() == 0 and gen.status() == 0
+    for x, y in zip(tuple(f) + tuple(g), tuple(fg) + tuple(gg)):
+        np.testing.assert_allclose(x.cpu().numpy(), y.cpu().numpy(), rtol=1e-3, atol=1e-4)

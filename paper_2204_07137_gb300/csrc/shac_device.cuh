@@ -367,7 +367,10 @@ __device__ __forceinline__ int chain_next(const DevModel& M, int i) { return __l
 // lk_joint_local: pose of link i in its parent's frame (joint frame times
 // joint motion: Rot(axis, q) for revolute, q axis for prismatic; the free
 // root's pose from its quaternion), written to the pose fields of link i's record.
-template <class Mem>
+// TO_WORK: write the local pose to the pose-cotangent slot of link i's work
+// record (its [R, P] layout; free in the forward pass) instead of its record,
+// for poses_by_rows.
+template <bool TO_WORK = false, class Mem>
 __device__ __forceinline__ void lk_joint_local(const DevModel& M, const Mem& w, int i) {
   const int jt = __ldg(M.jtype + i), s = __ldg(M.qs + i);
   M33 R;
@@ -382,8 +385,38 @@ __device__ __forceinline__ void lk_joint_local(const DevModel& M, const Mem& w, 
     if (jt == J_REV) R = mul(R, axis_angle(ax, w[M.o_Q + s]));
     else if (jt == J_PRIS) P = P + w[M.o_Q + s] * mul(R, ax);
   }
-  stm(w, lrec(M, i) + LR_R, R);
-  st3(w, lrec(M, i) + LR_P, P);
+  const int o = TO_WORK ? lwork(M, i) + LW_TP : lrec(M, i);
+  static_assert(LR_P == LR_R + 9, "a pose is R (9) then P (3)");
+  stm(w, o + LR_R, R);
+  st3(w, o + LR_P, P);
+}
+
+// World poses by rows (team form): the lane owning row r (lanes r, r + T, ...
+// for the three rows; a team of two lanes gives the first lane rows 0 and 2)
+// computes row r of R_i = R_p R_local and P_i[r] = P_p[r] + (row r of R_p) .
+// P_local for every link in ascending order (parents first; a root keeps its
+// local pose).  Row r of a link's pose depends only on row r of its parent's,
+// which the same lane wrote, so the lanes never wait for one another; the local
+// poses come from the work records (lk_joint_local<true>).
+template <class Mem>
+__device__ __forceinline__ void poses_by_rows(const DevModel& M, const Mem& w, int lane, int nl) {
+  for (int r = lane; r < 3; r += nl) {
+#pragma unroll
+    for (int i = 0; i < M.L; ++i) {
+      const int ol = lwork(M, i) + LW_TP, o = lrec(M, i);
+      const int p = link_parent(M, i);
+      V3 row = ld3(w, ol + LR_R + 3 * r);
+      float pr = w[ol + LR_P + r];
+      if (p >= 0) {
+        const int op = lrec(M, p);
+        const V3 rp = ld3(w, op + LR_R + 3 * r);
+        row = rp.x * ld3(w, ol + LR_R) + rp.y * ld3(w, ol + LR_R + 3) + rp.z * ld3(w, ol + LR_R + 6);
+        pr = w[op + LR_P + r] + dot(rp, ld3(w, ol + LR_P));
+      }
+      st3(w, o + LR_R + 3 * r, row);
+      w[o + LR_P + r] = pr;
+    }
+  }
 }
 
 // World pose, velocity and acceleration carried from a link to its child.
@@ -466,28 +499,10 @@ __device__ __forceinline__ void lk_kin(const DevModel& M, const Mem& w, int i, K
   c.R = R; c.P = P; c.Vw = Vw; c.Vv = Vv; c.aw = aw; c.av = av;
 }
 
-// Team form of sweep 1: only the world poses flow along the chains (lk_pose,
-// R_i = R_p R_local, P_i = P_p + R_p P_local, the parent's pose carried in
-// registers); the rest of lk_kin is a pass per link and two ancestor sums,
-// since V_i = V_p + u_i and A_i = A_p + V_i x u_i (the roots' A_p: -g) are
-// sums of terms of each link along its path from the root.
-struct PoseCarry {
-  M33 R;
-  V3 P;
-};
-template <class Mem>
-__device__ __forceinline__ void lk_pose(const DevModel& M, const Mem& w, int i, bool root, PoseCarry& c) {
-  M33 R = ldm(w, lrec(M, i) + LR_R);
-  V3 P = ld3(w, lrec(M, i) + LR_P);
-  if (!root) {
-    P = c.P + mul(c.R, P);
-    R = mul(c.R, R);
-  }
-  stm(w, lrec(M, i) + LR_R, R);
-  st3(w, lrec(M, i) + LR_P, P);
-  c.R = R;
-  c.P = P;
-}
+// Team form of sweep 1: the world poses by rows (poses_by_rows), the rest of
+// lk_kin a pass per link and two ancestor sums, since V_i = V_p + u_i and
+// A_i = A_p + V_i x u_i (the roots' A_p: -g) are sums of terms of each link
+// along its path from the root.
 // Link i's motion-subspace columns (as in lk_kin) and its joint velocity u_i,
 // the own term of V_i, stored in the V field and, for lk_bias_acc_own, in the
 // F_bar field (unused by the forward pass).
@@ -605,26 +620,11 @@ __device__ __forceinline__ void lk_local(const DevModel& M, const Mem& w, int i)
 // forces; then the muscle wrenches (their segments span two links).
 template <class Mem>
 __device__ void sw_forward(const DevModel& M, const Mem& w, int lane, int nl) {
-  for (int i = lane; i < M.L; i += nl) lk_joint_local(M, w, i);
-  team_sync(nl);
-  if (nl > 1) {   // a team: the poses along the chains, the rest per link and by ancestor sums
-    for (int l = 0; l < M.nlev; ++l) {
-      for (int ii = __ldg(M.lvl_ptr + l) + lane; ii < __ldg(M.lvl_ptr + l + 1); ii += nl) {
-        const int hd = __ldg(M.lvl_link + ii), tl = __ldg(M.chain_tail + hd), p = __ldg(M.parent + hd);
-        PoseCarry c;
-        if (p >= 0) {
-          c.R = ldm(w, lrec(M, p) + LR_R);
-          c.P = ld3(w, lrec(M, p) + LR_P);
-        }
-        bool root = p < 0;
-        for (int i = hd;; i = chain_next(M, i)) {
-          lk_pose(M, w, i, root, c);
-          root = false;
-          if (i == tl) break;
-        }
-      }
-      team_sync(nl);
-    }
+  if (nl > 1) {   // a team: poses by rows, the rest per link and by ancestor sums
+    for (int i = lane; i < M.L; i += nl) lk_joint_local<true>(M, w, i);
+    team_sync(nl);
+    poses_by_rows(M, w, lane, nl);
+    team_sync(nl);
     for (int i = lane; i < M.L; i += nl) lk_subspace_vel(M, w, i);
     team_sync(nl);
     ancestor_sums<6, true>(M, w, LR_V, lane, nl);
@@ -634,6 +634,7 @@ __device__ void sw_forward(const DevModel& M, const Mem& w, int lane, int nl) {
     ancestor_sums<6>(M, w, LW_A, lane, nl);
     team_sync(nl);
   } else {        // one thread: chain walks carrying pose, velocity and acceleration
+    for (int i = 0; i < M.L; ++i) lk_joint_local(M, w, i);
     for (int l = 0; l < M.nlev; ++l) {
       for (int ii = __ldg(M.lvl_ptr + l); ii < __ldg(M.lvl_ptr + l + 1); ++ii) {
         const int hd = __ldg(M.lvl_link + ii), tl = __ldg(M.chain_tail + hd);

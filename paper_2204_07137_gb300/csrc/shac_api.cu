@@ -102,7 +102,7 @@ static void compute_layout(shac_model* m) {
   take(d.o_SEGA, m->nseg);
   // free root: its six DOFs' reverse terms (velocity cotangent sums 6, then
   // one rotation-column share of 3 per DOF)
-  take(d.o_RDB, m->root_free ? 24 : 0);
+  take(d.o_RDB, m->root_free ? 18 : 0);   // the free root's six DOF shares of its rotation cotangent
   // partial muscle sums of (link, part) slots: at most max(32, L) slots (parts
   // = lanes / links when a team has at least two lanes per link, else 1),
   // 6 floats forward, 12 in reverse

@@ -25,14 +25,18 @@
 //
 // Every stage is written for a "team" of nl lanes working on one
 // environment: loops stride by nl and team_sync() separates dependent
-// phases.  Tree recursions are level sweeps in which one lane does all the
-// work of a link.  With nl = 1 (one environment per thread, PLAIN form) the loops
-// are the serial algorithm and team_sync() is a no-op; the BATCHED form runs
-// teams of 1..32 lanes inside a warp on shared-memory scratch.  Each phase
-// writes any given scratch slot from exactly one lane, so results do not
-// depend on the team size beyond floating-point reassociation of the sums
-// that a team performs in a different order (there is none: every
-// reduction below is a fixed-order gather).
+// phases.  With nl = 1 (one environment per thread, PLAIN form) the loops are
+// the serial algorithm, team_sync() is a no-op and the tree recursions are
+// chain walks with register carries; the BATCHED form runs teams of 1..32
+// lanes inside a warp on shared-memory scratch, where a team of two or more
+// lanes computes the tree recursions as per-lane tree sums (one component per
+// lane, links in a fixed order) and the world poses by rows.  Each phase
+// writes any given scratch slot from exactly one lane and every sum runs in a
+// fixed order, so a team's results do not depend on its size beyond the
+// dense stage (the register path needs nl >= nv, narrower teams use the
+// shared-memory stages) and the muscle wrenches (summed in as many partial
+// sums per link as the team has lanes per link); they differ from one
+// thread's chain walks by the reassociation of those sums.
 #pragma once
 #ifndef __CUDACC_RTC__
 #include <cuda_runtime.h>
@@ -290,10 +294,11 @@ __device__ __forceinline__ void si_mul(const Mem& w, int o, V3 xw, V3 xv, V3& yn
 
 // ================================================================= FORWARD ==
 //
-// Each link's work is one function called by one lane; a pass over the tree
-// is a level sweep (root first or leaves first) with one team barrier per
-// level.  A forward substep is two sweeps plus the dense solve; the plain
-// form calls the same functions from one thread per environment.
+// Each link's work is one function called by one lane; the recursions over
+// the tree are tree sums and poses by rows (a team) or chain walks (one
+// thread).  A forward substep is the root-first part, the local pass, the
+// leaves-first sums and the dense solve; the plain form calls the same
+// functions from one thread per environment.
 
 __device__ __forceinline__ M33 com_inertia(const DevModel& M, int i) {
   const float* ic = M.icom + 6 * i;
@@ -351,18 +356,21 @@ __device__ __forceinline__ void lk_muscle_wrench(const DevModel& M, const Mem& w
 // Lanes per link in the per-link muscle sums (at most 32 (link, part) slots).
 __device__ __forceinline__ int muscle_parts(const DevModel& M, int nl) { return nl >= 2 * M.L ? nl / M.L : 1; }
 
-// Tree sweeps visit chains: maximal runs of links in which every link but the
-// last has exactly one child.  A lane walks its chain parent-first (root-first
-// sweeps) or child-first (leaves-first sweeps); one team barrier per chain level.
+// The chain walks of the PLAIN form (and of a one-lane team) visit chains:
+// maximal runs of links in which every link but the last has exactly one
+// child, walked parent-first (root-first sweeps) or child-first (leaves-first
+// sweeps) with the carried values in registers.  Teams use the tree sums and
+// the poses by rows instead.
 __device__ __forceinline__ int chain_next(const DevModel& M, int i) { return __ldg(M.ch_idx + __ldg(M.ch_ptr + i)); }
 
-// Sweep 1 is split into passes.  Only what flows down the tree - the world
-// pose, velocity and acceleration of the parent - is computed in the
-// root-first pass, and a lane walking a chain keeps the parent's values in
-// registers (KinCarry).  Everything local to a link runs with one lane per
-// link for all links at once: the joint's own transform before the
-// root-first pass (lk_joint_local), the inertia, contacts and local force
-// after it (lk_local).
+// Sweep 1 is split into passes.  Everything local to a link runs with one
+// lane per link for all links at once: the joint's own transform before the
+// root-first part (lk_joint_local), the inertia, contacts and local force
+// after it (lk_local).  In between, what flows down the tree - the world pose,
+// velocity and acceleration of the parent: a team computes the poses by rows
+// (poses_by_rows) and the velocities and accelerations as ancestor sums of
+// per-link terms; a single thread (PLAIN form) walks the chains keeping the
+// parent's values in registers (KinCarry, lk_kin).
 //
 // lk_joint_local: pose of link i in its parent's frame (joint frame times
 // joint motion: Rot(axis, q) for revolute, q axis for prismatic; the free
@@ -616,8 +624,9 @@ __device__ __forceinline__ void lk_local(const DevModel& M, const Mem& w, int i)
 
 // Sweep 1: one lane per link the joint transforms; root first the world
 // poses, subspaces, velocities and Newton-Euler accelerations (qdd = 0) of
-// every link; one lane per link the inertias, contact forces and local
-// forces; then the muscle wrenches (their segments span two links).
+// every link (a team: poses by rows, per-link terms and ancestor sums; one
+// thread: chain walks); one lane per link the inertias, contact forces and
+// local forces; then the muscle wrenches (their segments span two links).
 template <class Mem>
 __device__ void sw_forward(const DevModel& M, const Mem& w, int lane, int nl) {
   if (nl > 1) {   // a team: poses by rows, the rest per link and by ancestor sums
@@ -1464,7 +1473,7 @@ struct BwdCarry {
   M33 tR;
 };
 
-// Adjoint sweep 2 (leaves first) at link i: gather the children (total
+// Adjoint sweep 2 (leaves first), chain form (one thread), at link i: gather the children (total
 // forces, A_bar, V_bar, kinematic cotangents; inside a chain the only child
 // is the link walked before, carried in g), reverse the Newton-Euler
 // accelerations and velocities and the motion subspaces, and pass the pose
@@ -1647,7 +1656,7 @@ __device__ __forceinline__ void root_dof_terms(const DevModel& M, const Mem& w, 
   w[M.o_QDB + d] += dot(sw, uw) + dot(sv, uv);
   const V3 sbw = wd * Fn + qdd * an + qd * uw;
   const V3 sbv = wd * Ff + qdd * af + qd * uv;
-  st3(w, M.o_RDB + 6 + 3 * d, d < 3 ? sbw + cross(sbv, ld3(w, lrec(M, 0) + LR_P)) : sbv);
+  st3(w, M.o_RDB + 3 * d, d < 3 ? sbw + cross(sbv, ld3(w, lrec(M, 0) + LR_P)) : sbv);
 }
 
 // q_bar of link i's joint from its final pose cotangents: revolute
@@ -1668,7 +1677,7 @@ __device__ __forceinline__ void lk_adj_qbar(const DevModel& M, const Mem& w, int
   if (jt == J_FREE) {   // the root origin is the reference point: no position cotangent here
 #pragma unroll
     for (int k = 0; k < 3; ++k) {   // the six DOF terms' shares, column k from DOFs k and 3 + k
-      const V3 a = ld3(w, M.o_RDB + 6 + 3 * k), b = ld3(w, M.o_RDB + 6 + 3 * (3 + k));
+      const V3 a = ld3(w, M.o_RDB + 3 * k), b = ld3(w, M.o_RDB + 3 * (3 + k));
       Rb.m[k] += a.x; Rb.m[3 + k] += a.y; Rb.m[6 + k] += a.z;
       Rb.m[k] += b.x; Rb.m[3 + k] += b.y; Rb.m[6 + k] += b.z;
     }

@@ -155,3 +155,43 @@ def long_chain(n_hinges):
     nv = 6 + n_hinges
     return b.finish(act_dof=list(range(6, nv)), act_gear=[5.0] * n_hinges, dt=I.CONTROL_DT, substeps=4,
                     armature=0.1, damping=0.1, root_z=5.0)
+
+
+def forest():
+    """A model with two roots and a branching subtree: a cart-pole (prismatic
+    root, hinge), and a second root hinged to the world carrying a two-hinge
+    branch that ends in a fixed-jointed body with a contact sphere touching
+    the ground, plus a prismatic slider on the first hinge; a joint limit on
+    the branch's second hinge.  nq = nv = 5."""
+    b = I._Builder("forest")
+    cart = b.link(-1, I.PRISMATIC, axis=(1, 0, 0), mass=1.0, inertia=np.diag([0.01, 0.01, 0.01]))
+    b.link(cart, I.REVOLUTE, axis=(0, 1, 0), mass=0.2, com=(0, 0, 0.4), inertia=np.diag([0.01, 0.01, 1e-4]))
+    m, c, J = I.capsule_mass_inertia(0.04, (0, 0, 0), (0, 0, -0.5), 1000.0)
+    h0 = b.link(-1, I.REVOLUTE, axis=(0, 1, 0), pos=(1.0, 0, 1.0), mass=m, com=c, inertia=J)
+    h1 = b.link(h0, I.REVOLUTE, axis=(1, 0, 0), pos=(0, 0, -0.5), mass=m, com=c, inertia=J, limit=(-0.15, 0.15))
+    tip = b.link(h1, I.FIXED, pos=(0, 0, -0.5), quat=(0, 0, 0.3826834, 0.9238795), mass=0.3, com=(0.05, 0, 0),
+                 inertia=np.diag([1e-3, 1e-3, 1e-3]))
+    b.link(h0, I.PRISMATIC, axis=(0, 0, 1), pos=(0.1, 0, -0.2), mass=0.2, inertia=np.diag([1e-3, 1e-3, 1e-3]))
+    b.contact(tip, (0, 0, 0.05), 0.08)
+    return b.finish(act_dof=[0, 2, 3], act_gear=[50.0, 10.0, 10.0], dt=I.CONTROL_DT, substeps=4, ke=5e3, kd=100.0,
+                    kt=50.0, mu=0.5, k_limit=1e3, armature=0.05, damping=0.05, rw_q=[0.1] * 5)
+
+
+def forest_trees():
+    """The two trees of forest() as models of their own (the cart-pole part
+    and the hinged branch), with the same links, joints, contact, limit and
+    actuation; a step of forest() is a step of each."""
+    a = I._Builder("forest_a")
+    cart = a.link(-1, I.PRISMATIC, axis=(1, 0, 0), mass=1.0, inertia=np.diag([0.01, 0.01, 0.01]))
+    a.link(cart, I.REVOLUTE, axis=(0, 1, 0), mass=0.2, com=(0, 0, 0.4), inertia=np.diag([0.01, 0.01, 1e-4]))
+    b = I._Builder("forest_b")
+    m, c, J = I.capsule_mass_inertia(0.04, (0, 0, 0), (0, 0, -0.5), 1000.0)
+    h0 = b.link(-1, I.REVOLUTE, axis=(0, 1, 0), pos=(1.0, 0, 1.0), mass=m, com=c, inertia=J)
+    h1 = b.link(h0, I.REVOLUTE, axis=(1, 0, 0), pos=(0, 0, -0.5), mass=m, com=c, inertia=J, limit=(-0.15, 0.15))
+    tip = b.link(h1, I.FIXED, pos=(0, 0, -0.5), quat=(0, 0, 0.3826834, 0.9238795), mass=0.3, com=(0.05, 0, 0),
+                 inertia=np.diag([1e-3, 1e-3, 1e-3]))
+    b.link(h0, I.PRISMATIC, axis=(0, 0, 1), pos=(0.1, 0, -0.2), mass=0.2, inertia=np.diag([1e-3, 1e-3, 1e-3]))
+    b.contact(tip, (0, 0, 0.05), 0.08)
+    kw = dict(dt=I.CONTROL_DT, substeps=4, ke=5e3, kd=100.0, kt=50.0, mu=0.5, k_limit=1e3, armature=0.05, damping=0.05)
+    return (a.finish(act_dof=[0], act_gear=[50.0], rw_q=[0.1] * 2, **kw),
+            b.finish(act_dof=[0, 1], act_gear=[10.0, 10.0], rw_q=[0.1] * 3, **kw))

@@ -461,3 +461,20 @@ def test_planar_reward_shapes(oracle_mod):
     qd = np.zeros((2, 6)); qd[:, 0] = 1.5
     _, _, r = oh.step(q, qd, np.full((2, 3), 0.5))
     np.testing.assert_allclose(r, [1.5 - 2.0 - (0.2 / (math.pi / 6)) ** 2 - 0.075, 1.5 + 0.3 - 0.075], atol=1e-6)
+
+
+def test_oracle_forest_steps_as_its_separate_trees(oracle_mod):
+    """A model of two trees hanging from the world (parent -1 past link 0):
+    its step equals the step of each tree as a model of its own, the reward
+    their sum (the trees share nothing but the ground)."""
+    from helpers import forest, forest_trees, seeded_case
+    m = forest()
+    ma, mb = forest_trees()
+    for seed, kind in ((0, "initial"), (1, "random")):
+        q, qd, a = seeded_case(m, 5, seed, kind)
+        rq, rqd, rr = oracle_mod.Oracle(m).step(q.T, qd.T, a.T)
+        qa, qda, ra = oracle_mod.Oracle(ma).step(q[:2].T, qd[:2].T, a[:1].T)
+        qb, qdb, rb = oracle_mod.Oracle(mb).step(q[2:].T, qd[2:].T, a[1:].T)
+        np.testing.assert_allclose(rq, np.concatenate([qa, qb], 1), rtol=1e-12, atol=1e-12)
+        np.testing.assert_allclose(rqd, np.concatenate([qda, qdb], 1), rtol=1e-12, atol=1e-12)
+        np.testing.assert_allclose(rr, ra + rb, rtol=1e-12, atol=1e-12)

@@ -332,8 +332,10 @@ def h_sweep_main(args):
     """Window-length study (the paper's horizon study: every variant draws
     the same number of samples per learning episode, N x h fixed): for each
     h, N = samples // h environments run the graph-captured forward + adjoint
-    window (window tape kept); one JSON line with env-steps/s, ms per window and
-    the kernel split per h.  L2 flushed before each timed window."""
+    window (window tape kept, the kernels specialised for the model unless
+    --no-specialize); one JSON line with env-steps/s, ms per window and the
+    kernel split per h (medians of the timed windows).  L2 flushed before each
+    timed window."""
     import torch
     from paper_2204_07137_gb300 import build, inputs as I
     from paper_2204_07137_gb300.sim import Simulator
@@ -348,6 +350,8 @@ def h_sweep_main(args):
         N = max(1, args.samples // h)
         sim = Simulator([(model, N)], form="batched", h_max=h)
         sim.set_window_tape(True)
+        if not args.no_specialize:
+            sim.specialize()
         q0, qd0 = (torch.from_numpy(np.ascontiguousarray(x.reshape(-1))).to(dev) for x in I.initial_state(model, N, 0))
         act = torch.from_numpy(I.window_actions(model, N, h, 0).reshape(h, -1)).to(dev).contiguous()
         rbar = torch.full((h, N), 1.0 / (N * h), device=dev)
@@ -371,7 +375,7 @@ def h_sweep_main(args):
                                                                     stream=stream))):
                 for _ in range(args.warmup):
                     fn()
-                total = 0.0
+                ts = []
                 for _ in range(args.steps):
                     flush.zero_()
                     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -379,14 +383,15 @@ def h_sweep_main(args):
                     fn()
                     e1.record(stream)
                     e1.synchronize()
-                    total += e0.elapsed_time(e1)
-                times[name] = total / args.steps
+                    ts.append(e0.elapsed_time(e1))
+                times[name] = float(np.median(ts))
         assert sim.status() == 0 and torch.isfinite(a[2]).all()
         rows.append({"h": h, "n_envs": N, "env_steps_per_s": N * h / (times["window"] * 1e-3),
                      "ms_per_window": times["window"], "ms_forward": times["forward"], "ms_adjoint": times["adjoint"],
                      "lanes_per_env": sim.get_launch(0)[0]})
         del sim
     print(json.dumps({"study": "window length h, N x h fixed", "model": model.name, "samples": args.samples,
+                      "kernels": "generic" if args.no_specialize else "model-specialised",
                       "dtype": "f32", "data": "synthetic", "rows": rows}), flush=True)
 
 

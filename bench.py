@@ -98,8 +98,9 @@ def fp32_peak_tflops(n_sms: int, sm_mhz: float) -> float:
 
 
 def measured_hbm_gbs():
-    """Measured HBM copy bandwidth of this machine's GPUs (MEASURED_PEAKS.json,
-    written next to this file by the harness), else the fallback figure."""
+    """Measured HBM copy bandwidth (MEASURED_PEAKS.json next to this file: a
+    STREAM-style copy measured on GB300s of the same kind), else the fallback
+    figure."""
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             return float(json.load(f)["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"

@@ -89,7 +89,7 @@ def algo_bytes_per_env_step(model):
 # adjoint's traffic is mostly its per-step substep records (about 91 MB per
 # step for 2048 environments) written back from L2 as they are replaced step
 # after step.
-TRAFFIC_BYTES_PER_LAUNCH = {"ant-2048": {"forward": 2.406912e6 + 0.0, "adjoint_recompute": 201.617408e6 + 2303.124992e6,
+TRAFFIC_BYTES_PER_LAUNCH = {"ant-2048": {"forward": 2.407168e6 + 0.0, "adjoint_recompute": 201.74336e6 + 2316.516608e6,
                                          "adjoint_tape": None}}
 
 

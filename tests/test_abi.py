@@ -77,3 +77,29 @@ def test_product_path_does_not_use_the_oracle():
     for fn in os.listdir(pkg):
         if fn.endswith(".py"):
             assert not pat.search(open(os.path.join(pkg, fn)).read()), fn
+
+
+def header_arities():
+    """Parameter count of every declaration in include/shacsim.h."""
+    src = open(os.path.join(ROOT, "include", "shacsim.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    out = {}
+    for name, params in re.findall(r"\b(shac_[a-z_]+)\s*\(([^;{()]*)\)\s*;", src):
+        ps = [p for p in params.split(",") if p.strip()]
+        out[name] = 0 if len(ps) == 1 and ps[0].strip() == "void" else len(ps)
+    return out
+
+
+def test_binding_argument_lists_match_the_header(lib):
+    """Every declared call has its ctypes argument list, as long as the C
+    declaration's (a changed signature fails here instead of passing
+    mis-marshalled arguments)."""
+    from paper_2204_07137_gb300 import _lib
+    from paper_2204_07137_gb300 import build
+    L = _lib.load(build.LIB)
+    arity = header_arities()
+    assert sorted(arity) == header_functions()
+    for name, n in arity.items():
+        argtypes = getattr(L, name).argtypes
+        assert argtypes is not None, f"{name}: no argtypes in the binding"
+        assert len(argtypes) == n, f"{name}: binding passes {len(argtypes)} arguments, the header declares {n}"
